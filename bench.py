@@ -1,0 +1,375 @@
+"""Benchmark of the full Tectonic pass (Algorithm 1 on one GPU).
+
+One step = one full pass over a graph already resident in HBM: degree
+orientation, per-edge triangle counts, Tectonic similarity, pruning at
+theta = 1/10 with fused union-find hooking, component labels.  Default
+workload: R-MAT scale 26, edge factor 32, (a,b,c,d) = (0.57,0.19,0.19,0.05),
+seed 3, generated on the GPU (untimed input preparation).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded edge sample instead.  Under torchrun every rank runs its own replica
+(the path does not shard: replicas only) and rank 0 reports the total.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Tectonic pass edges/s (1 GB300, % HBM roofline)"
+UNIT = "edges/s"
+
+WORKLOADS = {
+    "rmat26": dict(kind="rmat", scale=26, edge_factor=32, seed=3, p=1, q=10,
+                   name="R-MAT scale 26, edge factor 32, (0.57,0.19,0.19,0.05), seed 3; Tectonic full pass at 1/10"),
+    "rmat20": dict(kind="rmat", scale=20, edge_factor=16, seed=2, p=1, q=10,
+                   name="R-MAT scale 20, edge factor 16, (0.57,0.19,0.19,0.05), seed 2; Tectonic full pass at 1/10"),
+    "sbm": dict(kind="sbm", p=3, q=50,
+                name="planted-partition SBM n=2000, 4x500, p_in=0.05, p_out=0.002, seed 1; Tectonic at 3/50"),
+}
+
+# DRAM bytes per launch of the triangle-count stage from an ncu capture, per
+# unit of algorithmic bytes, valid only for the support.cu it was taken on
+# (see profiles/).  None until a capture exists for the current source.
+TRAFFIC_CAPTURE = {"support_sha": None, "dram_per_alg_byte": None}
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def support_sha() -> str:
+    with open(os.path.join(ROOT, "paper_2412_12382_gb300", "csrc", "support.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks sampled every 200 ms while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={CLOCK_FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_workload(spec, device):
+    import numpy as np
+    import torch
+    if spec["kind"] == "rmat":
+        from graphgen.gpu import rmat_csr_gpu
+        off, col = rmat_csr_gpu(spec["scale"], spec["edge_factor"], seed=spec["seed"])
+        return off, col
+    from graphgen import planted_partition
+    off, col, _ = planted_partition(4, 500, 0.05, 0.002, seed=1)
+    return torch.from_numpy(off).to(device), torch.from_numpy(np.asarray(col)).to(device)
+
+
+def algorithmic_bytes(off, ooff, m):
+    """W = sum_v d-(v) d+(v) + m neighbour reads; B_alg = 4W + 36m + 16n (whole pass),
+    B_support = 4W + 8m (intersection reads + one read-modify-write per counter)."""
+    import torch
+    deg = off[1:] - off[:-1]
+    dplus = ooff[1:] - ooff[:-1]
+    W = int(((deg - dplus) * dplus).sum().item()) + m
+    n = off.numel() - 1
+    return W, 4 * W + 36 * m + 16 * n, 4 * W + 8 * m
+
+
+def oracle_sample_rate(off_h, col_h, p, q, target_s=12.0, seed=0):
+    """The oracle as it stands on a uniform sample of canonical edges: merge
+    counts (all host threads) + exact prune.  Returns (edges/s, sample, threads)."""
+    import numpy as np
+    import oracle as O
+    threads = O.threads_available()
+    n = len(off_h) - 1
+    rng = np.random.default_rng(seed)
+    deg = np.diff(off_h)
+    m = int(off_h[-1]) // 2
+
+    def sample(k):
+        # uniform over symmetric entries, keep the u < v copy -> uniform over edges
+        ks = rng.integers(0, len(col_h), size=2 * k)
+        rows = np.searchsorted(off_h, ks, side="right") - 1
+        cols = col_h[ks].astype(np.int64)
+        sel = rows < cols
+        return rows[sel][:k].astype(np.int32), cols[sel][:k].astype(np.int32)
+
+    k = 2000
+    total_e, total_t = 0, 0.0
+    while total_t < target_s:
+        eu, ev = sample(k)
+        t0 = time.perf_counter()
+        t, uni = O.edge_counts(off_h, col_h, eu, ev, nthreads=threads)
+        O.prune(O.TECTONIC, off_h, eu, ev, t, uni, p, q)
+        dt = time.perf_counter() - t0
+        total_e += len(eu)
+        total_t += dt
+        rate = len(eu) / max(dt, 1e-9)
+        k = int(min(max(k * 2, rate * 2.0), 50_000_000))
+    return total_e / total_t, total_e, threads, total_t
+
+
+def run_reference(args, spec, rank, world):
+    import numpy as np
+    import torch
+    if rank != 0:
+        return 0
+    dev = torch.device("cuda", 0) if torch.cuda.is_available() else None
+    if dev is None and spec["kind"] == "rmat" and spec["scale"] > 18:
+        print(json.dumps({"impl": "reference", "unavailable": "workload generator needs a GPU"}))
+        return 0
+    off, col = make_workload(spec, dev)
+    off_h = off.cpu().numpy().astype(np.int64)
+    col_h = col.cpu().numpy().astype(np.int32)
+    del off, col
+    m = int(off_h[-1]) // 2
+    import oracle as O
+    threads = O.threads_available()
+    for _ in range(args.warmup):
+        oracle_sample_rate(off_h, col_h, spec["p"], spec["q"], target_s=0.5)
+    times, edges = [], 0
+    for s in range(args.steps):
+        rate, k, thr, tt = oracle_sample_rate(off_h, col_h, spec["p"], spec["q"], target_s=6.0, seed=s)
+        times.append(tt)
+        edges += k
+    value = edges / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * m / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": spec["name"], "m": m, "n": len(off_h) - 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{edges} uniformly sampled edges over {args.steps} steps: merge "
+                                       "intersections + exact prune (components not included)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat26", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warning: fewer than 3 warm-up steps")
+    spec = WORKLOADS[args.workload]
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if args.impl == "reference":
+        rc = run_reference(args, spec, rank, world)
+        if dist is not None:
+            dist.destroy_process_group()
+        return rc
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU for --impl ours")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2412_12382_gb300 import TECTONIC, Graph
+    from paper_2412_12382_gb300 import build as libbuild
+    from paper_2412_12382_gb300 import tectonic as T
+    libbuild.build()
+
+    t0 = time.time()
+    off, col = make_workload(spec, dev)
+    torch.cuda.synchronize()
+    n = off.numel() - 1
+    nnz = col.numel()
+    m = nnz // 2
+    log(f"workload {args.workload}: n={n} m={m} nnz={nnz} built in {time.time() - t0:.1f}s")
+
+    g = Graph(off, col)
+    stream = g.stream
+    p, q = spec["p"], spec["q"]
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+
+    for _ in range(args.warmup):
+        g.full_pass(TECTONIC, p, q, labels=labels, count=False)
+    g.sync()
+    ooff, _ = g.oriented_csr()
+    W, B_alg, B_sup = algorithmic_bytes(off, ooff, m)
+    del ooff
+    # one set of stage events per timed step, recorded on the graph's stream
+    step_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = T.launch_count()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        start.record(stream)
+        for k in range(args.steps):
+            g.set_stage_events(step_ev[k])
+            g.full_pass(TECTONIC, p, q, labels=labels, count=False)
+        end.record(stream)
+        torch.cuda.synchronize()
+    launches = T.launch_count() - l0
+    g.sync()
+    stage_ms = [[e[i].elapsed_time(e[i + 1]) for e in step_ev] for i in range(4)]
+    total_ms = start.elapsed_time(end)
+    if dist is not None:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * m / (ms_per_step / 1e3)
+    _, ncomp = g.full_pass(TECTONIC, p, q, labels=labels, count=True)
+    g.set_stage_events([])
+
+    peak, peak_kind = load_peaks()
+    sup_ms = statistics.mean(stage_ms[1])
+    achieved = B_sup / (sup_ms / 1e3) / 1e9
+    traffic = None
+    if TRAFFIC_CAPTURE["support_sha"] == support_sha() and TRAFFIC_CAPTURE["dram_per_alg_byte"]:
+        traffic = TRAFFIC_CAPTURE["dram_per_alg_byte"] * B_sup
+    pass_gbs = B_alg / (ms_per_step / 1e3) / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        off_h = torch.empty(n + 1, dtype=torch.int64, pin_memory=True)
+        col_h = torch.empty(nnz, dtype=torch.int32, pin_memory=True)
+        off_h.copy_(off)
+        col_h.copy_(col)
+        lab_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        on, cn, ln = off_h.numpy(), col_h.numpy(), lab_h.numpy()
+        g.full_pass_host(on, cn, TECTONIC, p, q, ln)
+        k_e2e = max(1, min(args.steps, 3))
+        if dist is not None:
+            dist.barrier()
+        t1 = time.perf_counter()
+        for _ in range(k_e2e):
+            g.full_pass_host(on, cn, TECTONIC, p, q, ln)
+        e2e_s = (time.perf_counter() - t1) / k_e2e
+        if dist is not None:
+            tt = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": world * m / e2e_s, "unit": UNIT, "h2d_bytes_per_step": (n + 1) * 8 + nnz * 4,
+               "d2h_bytes_per_step": n * 4 + 8 * 16}
+        ok = np.array_equal(ln, labels.cpu().numpy())
+        if not ok:
+            raise SystemExit("host-buffer pass disagrees with the device pass")
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        off_np = off.cpu().numpy().astype(np.int64)
+        col_np = col.cpu().numpy().astype(np.int32)
+        rate, k, thr, tt = oracle_sample_rate(off_np, col_np, p, q, target_s=12.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"{k} uniformly sampled edges of the same graph: merge intersections (Sec. III-C) "
+                         f"+ exact prune, {tt:.1f} s on {thr} host threads; components not included"}
+        del off_np, col_np
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": spec["name"], "n": n, "m": m, "theta": f"{p}/{q}",
+                       "components": ncomp, "W": W,
+                       "l2": f"inputs larger than L2: CSR {nnz * 4 / 1e9:.2f} GB vs 0.129 GB",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "pass_alg_bytes": B_alg, "pass_alg_GBps": pass_gbs,
+                       "pass_frac_of_peak": pass_gbs / peak,
+                       "stage_ms": {"orient": statistics.mean(stage_ms[0]), "support": sup_ms,
+                                    "prune_hook": statistics.mean(stage_ms[2]),
+                                    "finish": statistics.mean(stage_ms[3])}},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "triangle-count stage (support kernels)",
+                         "alg_bytes_per_launch": B_sup, "peak_kind": peak_kind},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "gpu_launches_per_step": launches / args.steps, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    g.free()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

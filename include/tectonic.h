@@ -1,0 +1,187 @@
+/*
+ * tectonic.h -- C ABI of the GB300 (sm_103a) motif-based community detection
+ * library (Chen & Tsourakakis, "Parallel Motif-Based Community Detection",
+ * arXiv 2412.12382).
+ *
+ * The library runs Algorithm 1 of the paper on one GPU: per-edge triangle
+ * counts t(u,v) and wedge counts (Sec. I, "Notations"), the Tectonic and TW
+ * similarities (Table 1, Eq. 1), pruning of every edge whose similarity is
+ * below a rational threshold delta = p/q, and the connected components of what
+ * is left.  Components are also computed for many thresholds at once.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - Every call returns a tec_status; TEC_OK is 0.  tec_last_error() gives a
+ *   human-readable message for the calling thread's last failure.  No C++
+ *   exception crosses this interface.
+ * - Graphs: undirected, simple (no self-loops, no duplicate edges), stored as a
+ *   symmetric CSR with both directions of every edge, rows sorted ascending,
+ *   vertices 0..n-1 (n < 2^31), row offsets int32 or int64, column ids int32.
+ *   m = nnz / 2 undirected edges.
+ * - Canonical edge order: edge e in [0, m) is the e-th pair (u, v), u < v, in
+ *   lexicographic order, i.e. the upper-triangle entries of the CSR row by
+ *   row.  Every per-edge output (t, wedge, weights, keep mask) uses it.
+ * - Pointers are DEVICE pointers unless a flag or the parameter's description
+ *   says host.  Outputs go into caller-allocated buffers of the documented
+ *   size; the library never frees caller memory.
+ * - A tec_graph owns a copy of the input CSR and all of its own scratch; the
+ *   caller may free its input buffers as soon as tec_graph_load returns.
+ *   Internal memory is released by tec_graph_free.
+ * - Work is issued asynchronously on the graph's CUDA stream (a cudaStream_t
+ *   passed as void*; NULL is the legacy default stream).  A call that returns
+ *   a host scalar (kept count, number of components) waits for that stream.
+ *   Device-side failures (a capped loop that ran out, an invalid CSR found by
+ *   validation) are recorded in a device status word and reported by the next
+ *   call that waits, or by tec_sync.
+ * - A tec_graph is not thread-safe: one host thread at a time per graph.
+ */
+#ifndef TECTONIC_H
+#define TECTONIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tec_status {
+    TEC_OK = 0,
+    TEC_EINVAL = 1,     /* a bad argument (NULL pointer, size out of range, q <= 0) */
+    TEC_ENOMEM = 2,     /* a device or host allocation failed */
+    TEC_ECUDA = 3,      /* a CUDA runtime call failed; the message names it */
+    TEC_ETIMEOUT = 4,   /* a bounded device loop hit its cap; the graph stays usable */
+    TEC_EOVERFLOW = 5,  /* a size or threshold does not fit the checked integer width */
+    TEC_EBADGRAPH = 6,  /* validation found an unsorted row, self-loop, duplicate or asymmetry */
+    TEC_ESTATE = 7      /* a call needs a step that has not been run (e.g. components before prune) */
+} tec_status;
+
+/* Similarity functions of Table 1. */
+typedef enum tec_measure {
+    TEC_TECTONIC = 0,   /* t(u,v) / (deg u + deg v) */
+    TEC_TW = 1          /* t(u,v) - wedge(u,v) = 3 t(u,v) + 2 - deg u - deg v (Eq. 1) */
+} tec_measure;
+
+/* tec_graph_load flags */
+#define TEC_HOST_PTR 0x1u   /* row_off / col are host pointers (pinned or pageable) */
+#define TEC_VALIDATE 0x2u   /* check the CSR invariants on the device; TEC_EBADGRAPH if violated */
+
+typedef struct tec_graph tec_graph;
+
+/* Library version as 10000*major + 100*minor + patch. */
+int tec_version(void);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated to
+ * len) into buf and returns its full length.  buf may be NULL when len is 0. */
+size_t tec_last_error(char *buf, size_t len);
+
+/* ---------------------------------------------------------------- graphs */
+
+/* Creates an empty graph with room for n_cap vertices and nnz_cap CSR entries
+ * (2 x undirected edges), allocating all device memory a pass needs on the
+ * current CUDA device.  stream: cudaStream_t (void*) that every later call on
+ * this graph uses.  TEC_ENOMEM if the device lacks memory. */
+tec_status tec_graph_create(int64_t n_cap, int64_t nnz_cap, void *stream, tec_graph **out);
+
+/* Loads a symmetric CSR (n vertices, nnz = 2m entries) into g, replacing any
+ * previous graph and its results.  row_off: n+1 offsets, int64 if off_is_i64
+ * else int32; col: nnz int32 ids.  flags: TEC_HOST_PTR, TEC_VALIDATE.
+ * TEC_EINVAL if n > n_cap or nnz > nnz_cap; TEC_EBADGRAPH under TEC_VALIDATE
+ * (waits for the stream).  Vertex degrees deg(u) = row lengths are computed
+ * here. */
+tec_status tec_graph_load(tec_graph *g, const void *row_off, int off_is_i64, const int32_t *col,
+                          int64_t n, int64_t nnz, uint32_t flags);
+
+/* tec_graph_create with exactly the needed capacity, then tec_graph_load. */
+tec_status tec_graph_upload(const void *row_off, int off_is_i64, const int32_t *col, int64_t n,
+                            int64_t nnz, uint32_t flags, void *stream, tec_graph **out);
+
+/* Waits for the graph's stream, frees every internal buffer and the handle. */
+tec_status tec_graph_free(tec_graph *g);
+
+/* Host scalars: vertex count and undirected edge count of the loaded graph. */
+tec_status tec_graph_info(const tec_graph *g, int64_t *n, int64_t *m);
+
+/* Waits for the graph's stream and reports any device-side failure recorded
+ * since the last wait (TEC_ETIMEOUT, TEC_EBADGRAPH), clearing it. */
+tec_status tec_sync(tec_graph *g);
+
+/* ---------------------------------------------------------------- steps */
+
+/* Degree-ordered orientation (Sec. II cites Shun & Tangwongsan for ranking by
+ * degree): keeps u -> v iff (deg u, u) < (deg v, v), so each undirected edge
+ * is stored once and every out-row stays sorted.  Needed by every later step;
+ * the steps below run it themselves when it has not been run. */
+tec_status tec_orient(tec_graph *g);
+
+/* Per-edge triangle counts t(u,v) = |N(u) n N(v)| (Sec. I) for all m edges,
+ * kept on the device for the steps below (Sec. III-C computes the same
+ * quantity by one merge per edge; here every triangle is listed once from its
+ * lowest-ranked vertex and credited to its three edges). */
+tec_status tec_support(tec_graph *g);
+
+/* Canonical edge list: u_out[e] < v_out[e], m entries each (device). */
+tec_status tec_edge_list(tec_graph *g, int32_t *u_out, int32_t *v_out);
+
+/* t(u,v) into t_out[m] and, if wedge_out is not NULL,
+ * wedge(u,v) = |N(u) u N(v)| - t(u,v) - 2 = deg u + deg v - 2 t(u,v) - 2
+ * into wedge_out[m] (Sec. I), both uint32 in canonical order (device). */
+tec_status tec_edge_support(tec_graph *g, uint32_t *t_out, uint32_t *wedge_out);
+
+/* Similarity of every edge as float64 in canonical order (device):
+ * TEC_TECTONIC: t / (deg u + deg v), one correctly rounded IEEE division;
+ * TEC_TW: t - wedge, an integer, exactly representable. */
+tec_status tec_edge_weights(tec_graph *g, tec_measure measure, double *w_out);
+
+/* Algorithm 1, first step: keeps edge e iff sim(e) >= p/q, i.e. removes
+ * exactly the edges with sim(e) < delta.  Decided in exact integer arithmetic:
+ * Tectonic: t*q >= p*(deg u + deg v); TW: (3t + 2 - deg u - deg v)*q >= p.
+ * q must be > 0 (TEC_EINVAL); |p| and q must be < 2^62 (TEC_EOVERFLOW).
+ * keep_out (device, m bytes, canonical order) may be NULL; kept_out (HOST,
+ * may be NULL; waits when given) receives the number of kept edges.  The mask
+ * stays on the device for tec_components. */
+tec_status tec_prune(tec_graph *g, tec_measure measure, int64_t p, int64_t q, uint8_t *keep_out,
+                     int64_t *kept_out);
+
+/* Algorithm 1, second step: connected components of (V, kept edges) of the
+ * last tec_prune.  labels_out (device, n int32): the smallest vertex id of each
+ * vertex's component (an isolated vertex is its own label).  ncomp_out (HOST,
+ * may be NULL; waits when given): number of components.  TEC_ESTATE if no
+ * prune has run. */
+tec_status tec_components(tec_graph *g, int32_t *labels_out, int64_t *ncomp_out);
+
+/* Algorithm 1 end to end on the loaded graph: orientation, triangle counts,
+ * similarity, pruning at p/q and components, with pruning and the union-find
+ * hooking fused into one kernel.  Same outputs as tec_prune + tec_components
+ * (labels_out device, ncomp_out host or NULL). */
+tec_status tec_full_pass(tec_graph *g, tec_measure measure, int64_t p, int64_t q,
+                         int32_t *labels_out, int64_t *ncomp_out);
+
+/* The same pass from host memory to host memory: copies a host CSR into g
+ * (within its capacity), runs tec_full_pass and copies the labels back into
+ * labels_host (n int32, HOST).  Waits for completion. */
+tec_status tec_full_pass_host(tec_graph *g, const int64_t *row_off_host, const int32_t *col_host,
+                              int64_t n, int64_t nnz, tec_measure measure, int64_t p, int64_t q,
+                              int32_t *labels_host, int64_t *ncomp_out);
+
+/* Instrumentation: number of kernels this library has launched in this
+ * process so far (all graphs, all devices). */
+long long tec_launch_count(void);
+
+/* Instrumentation: up to 5 cudaEvent_t (as void*) that tec_full_pass and
+ * tec_full_pass_host record on the graph's stream before orientation, after
+ * orientation, after the triangle counts, after pruning with union-find
+ * hooking, and after the component labels.  count 0 turns it off.  The events
+ * stay owned by the caller and must outlive their use. */
+tec_status tec_set_stage_events(tec_graph *g, void *const *events, int count);
+
+/* Introspection: copies the degree-ordered oriented CSR (running tec_orient
+ * if needed) into ooff_out (device, n+1 int64) and ocol_out (device, m int32);
+ * either may be NULL.  Row u lists N+(u) ascending. */
+tec_status tec_oriented_csr(tec_graph *g, int64_t *ooff_out, int32_t *ocol_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TECTONIC_H */

@@ -1,0 +1,487 @@
+// C ABI entry points (include/tectonic.h): argument checks, graph memory,
+// step ordering and status reporting.  All device work is in the kernels of
+// orient.cu, support.cu, prune.cu, cc.cu and scan.cu.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <new>
+#include <vector>
+
+#include "tec_internal.cuh"
+
+namespace tec {
+
+static thread_local char g_err[1024];
+
+tec_status set_error(tec_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+void clear_error() { g_err[0] = '\0'; }
+
+static std::atomic<long long> g_launches{0};
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+namespace {
+
+constexpr int64_t MAX_N = ((int64_t)1 << 31) - 1;
+constexpr int64_t THRESH_LIMIT = (int64_t)1 << 62;
+
+// Makes the graph's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+tec_status dalloc(T **p, int64_t count, const char *what) {
+    *p = nullptr;
+    size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(e == cudaErrorMemoryAllocation ? TEC_ENOMEM : TEC_ECUDA,
+                         "cudaMalloc of %zu bytes for %s failed: %s", bytes, what, cudaGetErrorString(e));
+    }
+    return TEC_OK;
+}
+
+void free_graph_memory(tec_graph *g) {
+    void *ptrs[] = {g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->parent, g->vlist,
+                    g->flags, g->tile_cnt, g->tile_base, g->bsum, g->uoff, g->ucnt, g->ctr};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (g->ctr_host) cudaFreeHost(g->ctr_host);
+}
+
+// Copies the counter block to the host and turns status bits into an error.
+tec_status read_counters(tec_graph *g) {
+    TEC_CUDA(cudaMemcpyAsync(g->ctr_host, g->ctr, C_COUNT * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, g->stream));
+    TEC_CUDA(cudaStreamSynchronize(g->stream));
+    const unsigned long long st = g->ctr_host[C_STATUS];
+    if (st) {
+        TEC_CUDA(cudaMemsetAsync(&g->ctr[C_STATUS], 0, sizeof(unsigned long long), g->stream));
+        TEC_CUDA(cudaStreamSynchronize(g->stream));
+        if (st & ST_BADGRAPH) {
+            g->oriented = g->supported = g->pruned = g->hooked = false;
+            return set_error(TEC_EBADGRAPH, "the CSR is not a simple undirected graph with sorted rows");
+        }
+        g->pruned = g->hooked = false;
+        return set_error(TEC_ETIMEOUT, "a bounded device loop reached its iteration cap");
+    }
+    return TEC_OK;
+}
+
+tec_status reset_counter(tec_graph *g, int which) {
+    TEC_CUDA(cudaMemsetAsync(&g->ctr[which], 0, sizeof(unsigned long long), g->stream));
+    return TEC_OK;
+}
+
+tec_status ensure_oriented(tec_graph *g) {
+    if (g->oriented) return TEC_OK;
+    TEC_CUDA(launch_orient(g->off, g->col, g->deg, g->n, g->nnz, g->flags, g->tile_cnt, g->tile_base,
+                           g->bsum, g->ooff, g->ocol, g->m, g->ctr, g->stream));
+    g->oriented = true;
+    g->supported = g->pruned = g->hooked = false;
+    return TEC_OK;
+}
+
+tec_status ensure_support(tec_graph *g) {
+    TEC_TRY(ensure_oriented(g));
+    if (g->supported) return TEC_OK;
+    TEC_CUDA(launch_support(g->ooff, g->ocol, g->n, g->m, g->t, g->vlist, g->ctr, g->num_sms, g->stream));
+    g->supported = true;
+    g->pruned = g->hooked = false;
+    return TEC_OK;
+}
+
+tec_status ensure_uoff(tec_graph *g) {
+    if (g->uoff_valid) return TEC_OK;
+    if (!g->uoff) TEC_TRY(dalloc(&g->uoff, g->n_cap + 1, "canonical row offsets"));
+    if (!g->ucnt) TEC_TRY(dalloc(&g->ucnt, g->n_cap, "canonical row counts"));
+    TEC_CUDA(launch_upper_counts(g->off, g->col, g->n, g->ucnt, g->stream));
+    TEC_CUDA(scan_exclusive_i32(g->ucnt, g->n, g->uoff, g->bsum, g->stream));
+    g->uoff_valid = true;
+    return TEC_OK;
+}
+
+tec_status check_threshold(int measure, int64_t p, int64_t q) {
+    if (measure != TEC_TECTONIC && measure != TEC_TW) return set_error(TEC_EINVAL, "unknown measure %d", measure);
+    if (q <= 0) return set_error(TEC_EINVAL, "threshold denominator q must be positive (got %lld)", (long long)q);
+    if (q >= THRESH_LIMIT || p >= THRESH_LIMIT || p <= -THRESH_LIMIT)
+        return set_error(TEC_EOVERFLOW, "|p| and q must be below 2^62");
+    return TEC_OK;
+}
+
+tec_status stage_mark(tec_graph *g, int i) {
+    if (i < g->n_stage_ev && g->stage_ev[i]) TEC_CUDA(cudaEventRecord(g->stage_ev[i], g->stream));
+    return TEC_OK;
+}
+
+tec_status run_full_pass(tec_graph *g, int measure, int64_t p, int64_t q, int32_t *labels) {
+    g->oriented = g->supported = false;
+    TEC_TRY(stage_mark(g, 0));
+    TEC_TRY(ensure_oriented(g));
+    TEC_TRY(stage_mark(g, 1));
+    TEC_TRY(ensure_support(g));
+    TEC_TRY(stage_mark(g, 2));
+    TEC_TRY(reset_counter(g, C_KEPT));
+    TEC_TRY(reset_counter(g, C_NCOMP));
+    TEC_CUDA(launch_cc_init(g->parent, g->n, g->stream));
+    PruneArgs a{measure, p, q, true};
+    TEC_CUDA(launch_prune(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, a, g->keep, g->parent, g->ctr, g->stream));
+    g->pruned = g->hooked = true;
+    g->last_measure = measure;
+    g->last_p = p;
+    g->last_q = q;
+    TEC_TRY(stage_mark(g, 3));
+    TEC_CUDA(launch_cc_finish(g->parent, g->n, labels, g->ctr, g->stream));
+    TEC_TRY(stage_mark(g, 4));
+    return TEC_OK;
+}
+
+}  // namespace
+}  // namespace tec
+
+using namespace tec;
+
+extern "C" {
+
+int tec_version(void) { return 100; }
+
+size_t tec_last_error(char *buf, size_t len) {
+    size_t full = strlen(g_err);
+    if (buf && len) {
+        size_t c = full < len - 1 ? full : len - 1;
+        memcpy(buf, g_err, c);
+        buf[c] = '\0';
+    }
+    return full;
+}
+
+tec_status tec_graph_create(int64_t n_cap, int64_t nnz_cap, void *stream, tec_graph **out) {
+    clear_error();
+    if (!out) return set_error(TEC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_cap < 0 || n_cap > MAX_N) return set_error(TEC_EINVAL, "n_cap must be in [0, 2^31-1]");
+    if (nnz_cap < 0 || nnz_cap > (int64_t)1 << 40) return set_error(TEC_EINVAL, "nnz_cap out of range");
+    tec_graph *g = new (std::nothrow) tec_graph();
+    if (!g) return set_error(TEC_ENOMEM, "host allocation failed");
+    g->stream = (cudaStream_t)stream;
+    g->n_cap = n_cap;
+    g->nnz_cap = nnz_cap;
+    g->m_cap = nnz_cap / 2;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (e != cudaSuccess) {
+        delete g;
+        return set_error(TEC_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+    }
+    const int64_t ntiles = ceil_div(nnz_cap, TILE);
+    const int64_t mwords = ceil_div(g->m_cap, TILE) * (TILE / 32);
+    const int64_t scan_len = (n_cap + 1 > ntiles ? n_cap + 1 : ntiles);
+    tec_status s = TEC_OK;
+    if (s == TEC_OK) s = dalloc(&g->off, n_cap + 1, "row offsets");
+    if (s == TEC_OK) s = dalloc(&g->col, nnz_cap, "column ids");
+    if (s == TEC_OK) s = dalloc(&g->deg, n_cap, "degrees");
+    if (s == TEC_OK) s = dalloc(&g->ooff, n_cap + 1, "oriented offsets");
+    if (s == TEC_OK) s = dalloc(&g->ocol, g->m_cap, "oriented column ids");
+    if (s == TEC_OK) s = dalloc(&g->t, g->m_cap, "triangle counts");
+    if (s == TEC_OK) s = dalloc(&g->keep, mwords, "keep mask");
+    if (s == TEC_OK) s = dalloc(&g->parent, n_cap, "union-find parents");
+    if (s == TEC_OK) s = dalloc(&g->vlist, n_cap, "vertex work list");
+    if (s == TEC_OK) s = dalloc(&g->flags, ntiles * (TILE / 32), "orientation bits");
+    if (s == TEC_OK) s = dalloc(&g->tile_cnt, ntiles + 1, "tile counts");
+    if (s == TEC_OK) s = dalloc(&g->tile_base, ntiles + 1, "tile offsets");
+    if (s == TEC_OK) s = dalloc(&g->bsum, scan_bsum_size(scan_len), "scan partials");
+    if (s == TEC_OK) s = dalloc(&g->ctr, C_COUNT, "counters");
+    if (s == TEC_OK) {
+        e = cudaMallocHost((void **)&g->ctr_host, C_COUNT * sizeof(unsigned long long));
+        if (e != cudaSuccess) s = set_error(TEC_ENOMEM, "pinned host allocation failed: %s", cudaGetErrorString(e));
+    }
+    if (s == TEC_OK) {
+        e = cudaMemsetAsync(g->ctr, 0, C_COUNT * sizeof(unsigned long long), g->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(g->off, 0, sizeof(int64_t), g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) s = set_error(TEC_ECUDA, "initialisation failed: %s", cudaGetErrorString(e));
+    }
+    if (s != TEC_OK) {
+        free_graph_memory(g);
+        delete g;
+        return s;
+    }
+    *out = g;
+    return TEC_OK;
+}
+
+tec_status tec_graph_load(tec_graph *g, const void *row_off, int off_is_i64, const int32_t *col, int64_t n,
+                          int64_t nnz, uint32_t flags) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (n < 0 || n > g->n_cap) return set_error(TEC_EINVAL, "n=%lld exceeds the capacity %lld", (long long)n, (long long)g->n_cap);
+    if (nnz < 0 || nnz > g->nnz_cap) return set_error(TEC_EINVAL, "nnz=%lld exceeds the capacity %lld", (long long)nnz, (long long)g->nnz_cap);
+    if (nnz % 2) return set_error(TEC_EINVAL, "nnz must be even (both directions of every edge)");
+    if (n == 0 && nnz != 0) return set_error(TEC_EINVAL, "a graph without vertices has no edges");
+    if (!row_off && n > 0) return set_error(TEC_EINVAL, "row_off is NULL");
+    if (!col && nnz > 0) return set_error(TEC_EINVAL, "col is NULL");
+    if (!off_is_i64 && nnz > INT32_MAX) return set_error(TEC_EOVERFLOW, "int32 offsets cannot index %lld entries", (long long)nnz);
+    DeviceGuard dg(g->device);
+    cudaStream_t s = g->stream;
+    const bool host = (flags & TEC_HOST_PTR) != 0;
+    g->oriented = g->supported = g->pruned = g->hooked = g->uoff_valid = false;
+    g->n = g->nnz = g->m = 0;
+    if (n > 0) {
+        if (off_is_i64) {
+            TEC_CUDA(cudaMemcpyAsync(g->off, row_off, (size_t)(n + 1) * sizeof(int64_t),
+                                     host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+        } else if (host) {
+            const int32_t *o32 = (const int32_t *)row_off;
+            std::vector<int64_t> wide(o32, o32 + n + 1);
+            TEC_CUDA(cudaMemcpyAsync(g->off, wide.data(), wide.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+            TEC_CUDA(cudaStreamSynchronize(s));
+        } else {
+            TEC_CUDA(launch_widen_offsets((const int32_t *)row_off, n + 1, g->off, s));
+        }
+    } else {
+        TEC_CUDA(cudaMemsetAsync(g->off, 0, sizeof(int64_t), s));
+    }
+    if (nnz > 0)
+        TEC_CUDA(cudaMemcpyAsync(g->col, col, (size_t)nnz * sizeof(int32_t),
+                                 host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    TEC_CUDA(cudaMemsetAsync(g->ctr, 0, C_COUNT * sizeof(unsigned long long), s));
+    g->n = n;
+    g->nnz = nnz;
+    g->m = nnz / 2;
+    if (flags & TEC_VALIDATE) {
+        TEC_CUDA(launch_validate(g->off, g->col, n, nnz, g->ctr, s));
+        tec_status st = read_counters(g);
+        if (st == TEC_OK) {
+            TEC_CUDA(launch_validate_entries(g->off, g->col, n, nnz, g->ctr, s));
+            st = read_counters(g);
+        }
+        if (st != TEC_OK) {
+            g->n = g->nnz = g->m = 0;
+            return st;
+        }
+    }
+    TEC_CUDA(launch_degrees(g->off, n, g->deg, s));
+    if (host) TEC_CUDA(cudaStreamSynchronize(s));
+    return TEC_OK;
+}
+
+tec_status tec_graph_upload(const void *row_off, int off_is_i64, const int32_t *col, int64_t n, int64_t nnz,
+                            uint32_t flags, void *stream, tec_graph **out) {
+    clear_error();
+    if (!out) return set_error(TEC_EINVAL, "out is NULL");
+    *out = nullptr;
+    tec_graph *g = nullptr;
+    TEC_TRY(tec_graph_create(n, nnz, stream, &g));
+    tec_status s = tec_graph_load(g, row_off, off_is_i64, col, n, nnz, flags);
+    if (s != TEC_OK) {
+        char keep_msg[sizeof(g_err)];
+        memcpy(keep_msg, g_err, sizeof(g_err));
+        tec_graph_free(g);
+        memcpy(g_err, keep_msg, sizeof(g_err));
+        return s;
+    }
+    *out = g;
+    return TEC_OK;
+}
+
+tec_status tec_graph_free(tec_graph *g) {
+    clear_error();
+    if (!g) return TEC_OK;
+    DeviceGuard dg(g->device);
+    cudaStreamSynchronize(g->stream);
+    free_graph_memory(g);
+    delete g;
+    return TEC_OK;
+}
+
+tec_status tec_graph_info(const tec_graph *g, int64_t *n, int64_t *m) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    return TEC_OK;
+}
+
+tec_status tec_sync(tec_graph *g) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    DeviceGuard dg(g->device);
+    return read_counters(g);
+}
+
+tec_status tec_orient(tec_graph *g) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    DeviceGuard dg(g->device);
+    g->oriented = false;
+    return ensure_oriented(g);
+}
+
+tec_status tec_support(tec_graph *g) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    DeviceGuard dg(g->device);
+    g->supported = false;
+    return ensure_support(g);
+}
+
+tec_status tec_edge_list(tec_graph *g, int32_t *u_out, int32_t *v_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if ((!u_out || !v_out) && g->m > 0) return set_error(TEC_EINVAL, "output is NULL");
+    DeviceGuard dg(g->device);
+    TEC_TRY(ensure_uoff(g));
+    TEC_CUDA(launch_export(g->off, g->col, g->deg, g->ooff, g->ocol, nullptr, g->keep, g->n, g->nnz, g->uoff,
+                           u_out, v_out, nullptr, nullptr, nullptr, 0, nullptr, g->ctr, g->stream));
+    return TEC_OK;
+}
+
+tec_status tec_edge_support(tec_graph *g, uint32_t *t_out, uint32_t *wedge_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (!t_out && g->m > 0) return set_error(TEC_EINVAL, "t_out is NULL");
+    DeviceGuard dg(g->device);
+    TEC_TRY(ensure_support(g));
+    TEC_TRY(ensure_uoff(g));
+    TEC_CUDA(launch_export(g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->n, g->nnz, g->uoff,
+                           nullptr, nullptr, t_out, wedge_out, nullptr, 0, nullptr, g->ctr, g->stream));
+    return TEC_OK;
+}
+
+tec_status tec_edge_weights(tec_graph *g, tec_measure measure, double *w_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (measure != TEC_TECTONIC && measure != TEC_TW) return set_error(TEC_EINVAL, "unknown measure %d", (int)measure);
+    if (!w_out && g->m > 0) return set_error(TEC_EINVAL, "w_out is NULL");
+    DeviceGuard dg(g->device);
+    TEC_TRY(ensure_support(g));
+    TEC_TRY(ensure_uoff(g));
+    TEC_CUDA(launch_export(g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->n, g->nnz, g->uoff,
+                           nullptr, nullptr, nullptr, nullptr, w_out, (int)measure, nullptr, g->ctr, g->stream));
+    return TEC_OK;
+}
+
+tec_status tec_prune(tec_graph *g, tec_measure measure, int64_t p, int64_t q, uint8_t *keep_out,
+                     int64_t *kept_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    TEC_TRY(check_threshold((int)measure, p, q));
+    DeviceGuard dg(g->device);
+    TEC_TRY(ensure_support(g));
+    TEC_TRY(reset_counter(g, C_KEPT));
+    PruneArgs a{(int)measure, p, q, false};
+    TEC_CUDA(launch_prune(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, a, g->keep, g->parent, g->ctr, g->stream));
+    g->pruned = true;
+    g->hooked = false;
+    g->last_measure = (int)measure;
+    g->last_p = p;
+    g->last_q = q;
+    if (keep_out) {
+        TEC_TRY(ensure_uoff(g));
+        TEC_CUDA(launch_export(g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->n, g->nnz, g->uoff,
+                               nullptr, nullptr, nullptr, nullptr, nullptr, 0, keep_out, g->ctr, g->stream));
+    }
+    if (kept_out) {
+        TEC_TRY(read_counters(g));
+        *kept_out = (int64_t)g->ctr_host[C_KEPT];
+    }
+    return TEC_OK;
+}
+
+tec_status tec_components(tec_graph *g, int32_t *labels_out, int64_t *ncomp_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (!g->pruned) return set_error(TEC_ESTATE, "tec_components needs a tec_prune first");
+    if (!labels_out && g->n > 0) return set_error(TEC_EINVAL, "labels_out is NULL");
+    DeviceGuard dg(g->device);
+    if (!g->hooked) {
+        TEC_CUDA(launch_cc_init(g->parent, g->n, g->stream));
+        TEC_CUDA(launch_cc_hook(g->ooff, g->ocol, g->keep, g->n, g->m, g->parent, g->ctr, g->stream));
+        g->hooked = true;
+    }
+    TEC_TRY(reset_counter(g, C_NCOMP));
+    TEC_CUDA(launch_cc_finish(g->parent, g->n, labels_out, g->ctr, g->stream));
+    if (ncomp_out) {
+        TEC_TRY(read_counters(g));
+        *ncomp_out = (int64_t)g->ctr_host[C_NCOMP];
+    }
+    return TEC_OK;
+}
+
+tec_status tec_full_pass(tec_graph *g, tec_measure measure, int64_t p, int64_t q, int32_t *labels_out,
+                         int64_t *ncomp_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    TEC_TRY(check_threshold((int)measure, p, q));
+    if (!labels_out && g->n > 0) return set_error(TEC_EINVAL, "labels_out is NULL");
+    DeviceGuard dg(g->device);
+    TEC_TRY(run_full_pass(g, (int)measure, p, q, labels_out));
+    if (ncomp_out) {
+        TEC_TRY(read_counters(g));
+        *ncomp_out = (int64_t)g->ctr_host[C_NCOMP];
+    }
+    return TEC_OK;
+}
+
+tec_status tec_full_pass_host(tec_graph *g, const int64_t *row_off_host, const int32_t *col_host, int64_t n,
+                              int64_t nnz, tec_measure measure, int64_t p, int64_t q, int32_t *labels_host,
+                              int64_t *ncomp_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (!labels_host && n > 0) return set_error(TEC_EINVAL, "labels_host is NULL");
+    TEC_TRY(check_threshold((int)measure, p, q));
+    DeviceGuard dg(g->device);
+    TEC_TRY(tec_graph_load(g, row_off_host, 1, col_host, n, nnz, TEC_HOST_PTR));
+    TEC_TRY(run_full_pass(g, (int)measure, p, q, g->parent));
+    if (n > 0)
+        TEC_CUDA(cudaMemcpyAsync(labels_host, g->parent, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 g->stream));
+    TEC_TRY(read_counters(g));
+    if (ncomp_out) *ncomp_out = (int64_t)g->ctr_host[C_NCOMP];
+    return TEC_OK;
+}
+
+long long tec_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+tec_status tec_set_stage_events(tec_graph *g, void *const *events, int count) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (count < 0 || count > 5 || (count > 0 && !events)) return set_error(TEC_EINVAL, "0..5 events");
+    for (int i = 0; i < 5; ++i) g->stage_ev[i] = i < count ? (cudaEvent_t)events[i] : nullptr;
+    g->n_stage_ev = count;
+    return TEC_OK;
+}
+
+tec_status tec_oriented_csr(tec_graph *g, int64_t *ooff_out, int32_t *ocol_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    DeviceGuard dg(g->device);
+    TEC_TRY(ensure_oriented(g));
+    if (ooff_out)
+        TEC_CUDA(cudaMemcpyAsync(ooff_out, g->ooff, (size_t)(g->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                                 g->stream));
+    if (ocol_out && g->m > 0)
+        TEC_CUDA(cudaMemcpyAsync(ocol_out, g->ocol, (size_t)g->m * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                 g->stream));
+    return TEC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// Similarity, pruning and per-edge exports.
+//
+// Tectonic (Table 1) keeps oriented edge u->v iff t*q >= p*(deg u + deg v);
+// TW (Eq. 1) keeps it iff (3t + 2 - deg u - deg v)*q >= p, since
+// wedge = |N(u) u N(v)| - t - 2 = deg u + deg v - 2t - 2.  Algorithm 1 removes
+// only edges with sim < p/q, so equality keeps the edge.  Products fit int64
+// when |p|, q < 2^28; larger thresholds take the 128-bit path.
+//
+// The prune kernel streams the oriented edges in tiles of 2048, finds each
+// edge's source row by binary search in the tile's row range, writes one keep
+// bit per edge and, fused, can hook the endpoints of kept edges in the
+// union-find forest (the first phase of the components step).
+#include "tec_internal.cuh"
+#include "uf.cuh"
+
+namespace tec {
+namespace {
+
+constexpr int64_t NARROW_LIMIT = (int64_t)1 << 28;
+
+template <bool WIDE>
+__device__ __forceinline__ bool keep_edge(int measure, uint32_t tt, int64_t s, int64_t p, int64_t q) {
+    if (measure == TEC_TECTONIC) {
+        if (WIDE) return (__int128)tt * q >= (__int128)p * s;
+        return (int64_t)tt * q >= p * s;
+    }
+    const int64_t tw = 3 * (int64_t)tt + 2 - s;
+    if (WIDE) return (__int128)tw * q >= (__int128)p;
+    return tw * q >= p;
+}
+
+template <bool HOOK, bool WIDE>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_prune(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t, int64_t n,
+        int64_t m, int measure, int64_t p, int64_t q, uint32_t *keep, int32_t *parent,
+        unsigned long long *ctr) {
+    __shared__ int ws[TILE_THREADS / 32];
+    if (graph_bad(ctr)) return;
+    const int64_t k0 = (int64_t)blockIdx.x * TILE;
+    const int64_t klast = min(k0 + TILE, m) - 1;
+    const int64_t r0 = row_search(ooff, 0, n - 1, k0);
+    const int64_t r1 = row_search(ooff, r0, n - 1, klast);
+    const unsigned lane = lane_id();
+    int kept = 0;
+    for (int i = 0; i < TILE_ITEMS; ++i) {
+        const int64_t jw = k0 + (int64_t)i * TILE_THREADS + (threadIdx.x & ~31u);
+        const int64_t j = jw + lane;
+        bool kp = false;
+        if (j < m) {
+            const int64_t u = row_search(ooff, r0, r1, j);
+            const int32_t v = ocol[j];
+            const int64_t s = (int64_t)deg[u] + deg[v];
+            kp = keep_edge<WIDE>(measure, t[j], s, p, q);
+            if (HOOK && kp) uf_link(parent, (int32_t)u, v, ctr);
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, kp);
+        if (lane == 0 && jw < m) keep[jw >> 5] = b;
+        kept += kp ? 1 : 0;
+    }
+    kept = warp_sum(kept);
+    if (lane == 0) ws[threadIdx.x >> 5] = kept;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < TILE_THREADS / 32; ++w) tot += ws[w];
+        if (tot) atomicAdd(&ctr[C_KEPT], (unsigned long long)tot);
+    }
+}
+
+// Number of neighbours greater than u in each row (the canonical edges the row owns).
+__global__ void k_upper_counts(const int64_t *off, const int32_t *col, int64_t n, int32_t *cnt) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = off[u], hi = off[u + 1];
+        const int64_t end = hi;
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (col[mid] <= u) lo = mid + 1; else hi = mid;
+        }
+        cnt[u] = (int32_t)(end - lo);
+    }
+}
+
+// One thread per symmetric entry (u, v) with u < v: canonical id
+// e = uoff[u+1] - (off[u+1] - k); the oriented copy of the edge sits in the row
+// of the lower-ranked endpoint, found by binary search (rows are sorted).
+__global__ void __launch_bounds__(TILE_THREADS)
+k_export(const int64_t *off, const int32_t *col, const int32_t *deg, const int64_t *ooff,
+         const int32_t *ocol, const uint32_t *t, const uint32_t *keep, int64_t n, int64_t nnz,
+         const int64_t *uoff, int32_t *u_out, int32_t *v_out, uint32_t *t_out, uint32_t *wedge_out,
+         double *w_out, int w_measure, uint8_t *keep_out, unsigned long long *ctr) {
+    if (graph_bad(ctr)) return;
+    const int64_t k0 = (int64_t)blockIdx.x * TILE;
+    const int64_t klast = min(k0 + TILE, nnz) - 1;
+    const int64_t r0 = row_search(off, 0, n - 1, k0);
+    const int64_t r1 = row_search(off, r0, n - 1, klast);
+    const bool need_pos = t_out || wedge_out || w_out || keep_out;
+    for (int i = 0; i < TILE_ITEMS; ++i) {
+        const int64_t k = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
+        if (k >= nnz) break;
+        const int64_t u = row_search(off, r0, r1, k);
+        const int32_t v = col[k];
+        if (v <= u) continue;
+        const int64_t e = uoff[u + 1] - (off[u + 1] - k);
+        if (u_out) u_out[e] = (int32_t)u;
+        if (v_out) v_out[e] = v;
+        if (!need_pos) continue;
+        const int32_t du = deg[u], dv = deg[v];
+        const bool u_first = rank_less(du, u, dv, v);
+        const int64_t x = u_first ? u : v;
+        const int32_t y = u_first ? v : (int32_t)u;
+        int64_t lo = ooff[x], hi = ooff[x + 1];
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (ocol[mid] < y) lo = mid + 1; else hi = mid;
+        }
+        const int64_t pos = lo;
+        const uint32_t tt = t ? t[pos] : 0u;
+        const int64_t s = (int64_t)du + dv;
+        if (t_out) t_out[e] = tt;
+        if (wedge_out) wedge_out[e] = (uint32_t)(s - 2 * (int64_t)tt - 2);
+        if (w_out) {
+            if (w_measure == TEC_TECTONIC) w_out[e] = __ddiv_rn((double)tt, (double)s);
+            else w_out[e] = (double)(3 * (int64_t)tt + 2 - s);
+        }
+        if (keep_out) keep_out[e] = (uint8_t)((keep[pos >> 5] >> (pos & 31)) & 1u);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_prune(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
+                         int64_t n, int64_t m, PruneArgs a, uint32_t *keep, int32_t *parent,
+                         unsigned long long *ctr, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)ceil_div(m, TILE);
+    const bool wide = !(a.p > -NARROW_LIMIT && a.p < NARROW_LIMIT && a.q < NARROW_LIMIT);
+    if (a.hook) {
+        if (wide) k_prune<true, true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, a.measure, a.p, a.q, keep, parent, ctr);
+        else k_prune<true, false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, a.measure, a.p, a.q, keep, parent, ctr);
+    } else {
+        if (wide) k_prune<false, true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, a.measure, a.p, a.q, keep, parent, ctr);
+        else k_prune<false, false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, a.measure, a.p, a.q, keep, parent, ctr);
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_upper_counts(const int64_t *off, const int32_t *col, int64_t n, int32_t *cnt, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int64_t g = ceil_div(n, 256);
+    k_upper_counts<<<(unsigned)(g < 65536 ? g : 65536), 256, 0, s>>>(off, col, n, cnt);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(const int64_t *off, const int32_t *col, const int32_t *deg, const int64_t *ooff,
+                          const int32_t *ocol, const uint32_t *t, const uint32_t *keep, int64_t n,
+                          int64_t nnz, const int64_t *uoff, int32_t *u_out, int32_t *v_out,
+                          uint32_t *t_out, uint32_t *wedge_out, double *w_out, int w_measure,
+                          uint8_t *keep_out, unsigned long long *ctr, cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    k_export<<<(unsigned)ceil_div(nnz, TILE), TILE_THREADS, 0, s>>>(off, col, deg, ooff, ocol, t, keep, n, nnz,
+                                                                   uoff, u_out, v_out, t_out, wedge_out,
+                                                                   w_out, w_measure, keep_out, ctr);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace tec

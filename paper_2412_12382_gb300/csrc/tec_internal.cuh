@@ -1,0 +1,197 @@
+// Internal declarations of the tectonic library (not part of the C ABI).
+//
+// Device data layout of one loaded graph (all in HBM, owned by tec_graph):
+//   off   int64[n+1]   symmetric CSR row offsets (input copy)
+//   col   int32[nnz]   symmetric CSR column ids, rows ascending (input copy)
+//   deg   int32[n]     deg(u) = off[u+1] - off[u]
+//   ooff  int64[n+1]   oriented CSR offsets: row u holds N+(u) = {v in N(u) : (deg u, u) < (deg v, v)}
+//   ocol  int32[m]     oriented column ids, each row still ascending
+//   t     uint32[m]    triangle count of oriented edge j (same index as ocol)
+//   keep  uint32[ceil(m/32)] keep bit of oriented edge j after the last prune
+//   parent int32[n]    union-find forest; parent[x] <= x, roots are component minima
+// Every per-edge array is indexed by the oriented position j; exports map it to
+// the canonical (u < v, lexicographic) order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tectonic.h"
+
+namespace tec {
+
+// Device status bits (status word in the graph's counter block).
+constexpr uint32_t ST_TIMEOUT = 1u;   // a capped loop ran out
+constexpr uint32_t ST_BADGRAPH = 2u;  // the CSR violated an invariant
+
+// Counter block layout (unsigned long long each).
+enum Ctr : int {
+    C_STATUS = 0,
+    C_KEPT = 1,
+    C_NCOMP = 2,
+    C_NSMALL = 3,
+    C_NLARGE = 4,
+    C_NEXT = 5,
+    C_COUNT = 16
+};
+
+// Tile of CSR entries handled by one 256-thread block in the streaming passes.
+constexpr int TILE_THREADS = 256;
+constexpr int TILE_ITEMS = 8;
+constexpr int TILE = TILE_THREADS * TILE_ITEMS;   // 2048 entries, a multiple of 32
+
+// Rows with at most this many oriented neighbours are handled by one warp in
+// the support kernel; larger rows get a whole block.
+constexpr int SMALL_ROW = 32;
+// Oriented neighbours of one large row staged per shared-memory chunk.
+constexpr int LARGE_CHUNK = 8192;
+
+// Retry cap of one union-find link (each retry strictly lowers a root id, so a
+// correct run never needs more than n).
+constexpr int LINK_RETRY_CAP = 1 << 24;
+
+tec_status set_error(tec_status s, const char *fmt, ...);
+void clear_error();
+
+// Process-wide count of kernels this library has launched (tec_launch_count).
+void count_launches(int k);
+
+#define TEC_CUDA(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return ::tec::set_error(TEC_ECUDA, "%s failed: %s (%s:%d)", #call,                \
+                                    cudaGetErrorString(e_), __FILE__, __LINE__);             \
+    } while (0)
+
+#define TEC_TRY(expr)                                                                         \
+    do {                                                                                      \
+        tec_status s_ = (expr);                                                               \
+        if (s_ != TEC_OK) return s_;                                                          \
+    } while (0)
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------- launchers
+// Each returns cudaGetLastError() of its launches; all run on `s`.
+
+// scan.cu: exclusive prefix sum of `in[0..N)` into `out[0..N]` (out[N] = total).
+// `bsum` needs ceil(N / 2048) + 1 entries.
+cudaError_t scan_exclusive_i64(const int64_t *in, int64_t N, int64_t *out, int64_t *bsum, cudaStream_t s);
+cudaError_t scan_exclusive_i32(const int32_t *in, int64_t N, int64_t *out, int64_t *bsum, cudaStream_t s);
+int64_t scan_bsum_size(int64_t N);
+
+// orient.cu
+cudaError_t launch_widen_offsets(const int32_t *in, int64_t count, int64_t *out, cudaStream_t s);
+cudaError_t launch_degrees(const int64_t *off, int64_t n, int32_t *deg, cudaStream_t s);
+cudaError_t launch_validate(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz,
+                            unsigned long long *ctr, cudaStream_t s);
+cudaError_t launch_validate_entries(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz,
+                                    unsigned long long *ctr, cudaStream_t s);
+cudaError_t launch_orient(const int64_t *off, const int32_t *col, const int32_t *deg, int64_t n,
+                          int64_t nnz, uint32_t *flags, int64_t *tile_cnt, int64_t *tile_base,
+                          int64_t *bsum, int64_t *ooff, int32_t *ocol, int64_t m,
+                          unsigned long long *ctr, cudaStream_t s);
+
+// support.cu: t[j] for every oriented edge (t must be zeroed first; done inside).
+cudaError_t launch_support(const int64_t *ooff, const int32_t *ocol, int64_t n, int64_t m,
+                           uint32_t *t, int32_t *vlist, unsigned long long *ctr, int num_sms,
+                           cudaStream_t s);
+
+// prune.cu
+struct PruneArgs {
+    int measure;
+    int64_t p, q;
+    bool hook;          // also union the endpoints of every kept edge into `parent`
+};
+cudaError_t launch_prune(const int64_t *ooff, const int32_t *ocol, const int32_t *deg,
+                         const uint32_t *t, int64_t n, int64_t m, PruneArgs a, uint32_t *keep,
+                         int32_t *parent, unsigned long long *ctr, cudaStream_t s);
+cudaError_t launch_export(const int64_t *off, const int32_t *col, const int32_t *deg,
+                          const int64_t *ooff, const int32_t *ocol, const uint32_t *t,
+                          const uint32_t *keep, int64_t n, int64_t nnz, const int64_t *uoff,
+                          int32_t *u_out, int32_t *v_out, uint32_t *t_out, uint32_t *wedge_out,
+                          double *w_out, int w_measure, uint8_t *keep_out,
+                          unsigned long long *ctr, cudaStream_t s);
+cudaError_t launch_upper_counts(const int64_t *off, const int32_t *col, int64_t n, int32_t *cnt,
+                                cudaStream_t s);
+
+// cc.cu
+cudaError_t launch_cc_init(int32_t *parent, int64_t n, cudaStream_t s);
+cudaError_t launch_cc_hook(const int64_t *ooff, const int32_t *ocol, const uint32_t *keep,
+                           int64_t n, int64_t m, int32_t *parent, unsigned long long *ctr,
+                           cudaStream_t s);
+cudaError_t launch_cc_finish(int32_t *parent, int64_t n, int32_t *labels,
+                             unsigned long long *ctr, cudaStream_t s);
+
+// ---------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ int warp_sum(int x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Largest r in [lo, hi] with off[r] <= k (off non-decreasing, off[lo] <= k).
+__device__ __forceinline__ int64_t row_search(const int64_t *off, int64_t lo, int64_t hi, int64_t k) {
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo + 1) / 2;
+        if (off[mid] <= k) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Orientation order: u before v iff (deg u, u) < (deg v, v).
+__device__ __forceinline__ bool rank_less(int32_t du, int64_t u, int32_t dv, int64_t v) {
+    return du < dv || (du == dv && u < v);
+}
+
+__device__ __forceinline__ void flag_status(unsigned long long *ctr, uint32_t bit) {
+    atomicOr(&ctr[C_STATUS], (unsigned long long)bit);
+}
+
+__device__ __forceinline__ bool graph_bad(const unsigned long long *ctr) {
+    return (*(volatile const unsigned long long *)&ctr[C_STATUS] & ST_BADGRAPH) != 0;
+}
+
+}  // namespace tec
+
+// The opaque handle of the C ABI.
+struct tec_graph {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    int64_t n_cap = 0, nnz_cap = 0, m_cap = 0;
+    int64_t n = 0, nnz = 0, m = 0;
+
+    int64_t *off = nullptr;
+    int32_t *col = nullptr;
+    int32_t *deg = nullptr;
+    int64_t *ooff = nullptr;
+    int32_t *ocol = nullptr;
+    uint32_t *t = nullptr;
+    uint32_t *keep = nullptr;
+    int32_t *parent = nullptr;
+    int32_t *vlist = nullptr;
+    uint32_t *flags = nullptr;
+    int64_t *tile_cnt = nullptr;
+    int64_t *tile_base = nullptr;
+    int64_t *bsum = nullptr;
+    int64_t *uoff = nullptr;        // export only, allocated on first export
+    int32_t *ucnt = nullptr;        // export only
+    unsigned long long *ctr = nullptr;      // device counter block
+    unsigned long long *ctr_host = nullptr; // pinned mirror for reads
+
+    // pipeline state
+    bool oriented = false;
+    bool supported = false;
+    bool pruned = false;
+    bool hooked = false;            // parent already holds the kept-edge forest
+    bool uoff_valid = false;
+    cudaEvent_t stage_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int n_stage_ev = 0;
+    int last_measure = 0;
+    int64_t last_p = 0, last_q = 1;
+};

@@ -1,0 +1,44 @@
+// Lock-free union-find on int32 vertex ids (ECL-CC style: hooking of the larger
+// root under the smaller with compare-and-swap, intermediate pointer jumping).
+//
+// Invariant: parent[x] <= x.  Only roots are ever re-pointed, always to a
+// smaller root, so the root of every tree is the smallest id in it and the
+// final labels are the component minima.  Reads bypass L1 (__ldcg) so a thread
+// sees other SMs' hooks; a stale read only costs another retry.
+#pragma once
+
+#include "tec_internal.cuh"
+
+namespace tec {
+
+__device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x) {
+    int32_t cur = __ldcg(&parent[x]);
+    if (cur != x) {
+        int32_t prev = x, next;
+        while (cur > (next = __ldcg(&parent[cur]))) {
+            parent[prev] = next;   // any ancestor is a valid parent
+            prev = cur;
+            cur = next;
+        }
+    }
+    return cur;
+}
+
+// Each failed compare-and-swap means a root was hooked by another thread, so
+// the retry loop makes global progress; the cap only guards against a broken
+// forest and reports TEC_ETIMEOUT.
+__device__ __forceinline__ void uf_link(int32_t *parent, int32_t a, int32_t b, unsigned long long *ctr) {
+    int32_t ra = uf_find(parent, a), rb = uf_find(parent, b);
+    for (int it = 0; it < LINK_RETRY_CAP; ++it) {
+        if (ra == rb) return;
+        const int32_t hi = ra > rb ? ra : rb;
+        const int32_t lo = ra > rb ? rb : ra;
+        const int32_t old = atomicCAS(&parent[hi], hi, lo);
+        if (old == hi) return;
+        ra = uf_find(parent, old);
+        rb = uf_find(parent, lo);
+    }
+    flag_status(ctr, ST_TIMEOUT);
+}
+
+}  // namespace tec

@@ -1,0 +1,272 @@
+"""Python binding of the C ABI in include/tectonic.h (argument marshalling only).
+
+Every computation runs in the CUDA kernels of ``libtectonic.so``; this module
+only allocates output tensors with PyTorch, passes raw pointers and raises on
+a non-zero status.  There is no fallback: if the library is missing or no GPU
+is present, calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TECTONIC = 0
+TW = 1
+HOST_PTR = 0x1
+VALIDATE = 0x2
+
+STATUS_NAMES = {0: "TEC_OK", 1: "TEC_EINVAL", 2: "TEC_ENOMEM", 3: "TEC_ECUDA", 4: "TEC_ETIMEOUT",
+                5: "TEC_EOVERFLOW", 6: "TEC_EBADGRAPH", 7: "TEC_ESTATE"}
+
+
+class TectonicError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+
+SIGNATURES = {
+    "tec_version": ([], ctypes.c_int),
+    "tec_last_error": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_size_t),
+    "tec_graph_create": ([_I64, _I64, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "tec_graph_load": ([_P, _P, ctypes.c_int, _P, _I64, _I64, ctypes.c_uint32], ctypes.c_int),
+    "tec_graph_upload": ([_P, ctypes.c_int, _P, _I64, _I64, ctypes.c_uint32, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "tec_graph_free": ([_P], ctypes.c_int),
+    "tec_graph_info": ([_P, _PI64, _PI64], ctypes.c_int),
+    "tec_sync": ([_P], ctypes.c_int),
+    "tec_orient": ([_P], ctypes.c_int),
+    "tec_support": ([_P], ctypes.c_int),
+    "tec_edge_list": ([_P, _P, _P], ctypes.c_int),
+    "tec_edge_support": ([_P, _P, _P], ctypes.c_int),
+    "tec_edge_weights": ([_P, ctypes.c_int, _P], ctypes.c_int),
+    "tec_prune": ([_P, ctypes.c_int, _I64, _I64, _P, _PI64], ctypes.c_int),
+    "tec_components": ([_P, _P, _PI64], ctypes.c_int),
+    "tec_full_pass": ([_P, ctypes.c_int, _I64, _I64, _P, _PI64], ctypes.c_int),
+    "tec_full_pass_host": ([_P, _P, _P, _I64, _I64, ctypes.c_int, _I64, _I64, _P, _PI64], ctypes.c_int),
+    "tec_oriented_csr": ([_P, _P, _P], ctypes.c_int),
+    "tec_launch_count": ([], ctypes.c_longlong),
+    "tec_set_stage_events": ([_P, ctypes.POINTER(_P), ctypes.c_int], ctypes.c_int),
+}
+
+
+def library_path() -> str:
+    return _build.library_path()
+
+
+def load_library(build_if_missing: bool = False):
+    """Loads libtectonic.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(f"CUDA library not built ({path}); run paper_2412_12382_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load_library().tec_launch_count())
+
+
+def last_error() -> str:
+    lib = load_library()
+    buf = ctypes.create_string_buffer(1024)
+    lib.tec_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def check(status: int):
+    if status != 0:
+        raise TectonicError(status, last_error())
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _require_cuda():
+    torch = _torch()
+    if not torch.cuda.is_available():
+        raise RuntimeError("the tectonic library needs a CUDA GPU; none is available")
+    return torch
+
+
+class Graph:
+    """A graph resident on the GPU (a ``tec_graph``).
+
+    ``off`` / ``col``: symmetric CSR, either CUDA tensors (int64 or int32
+    offsets, int32 ids) or numpy arrays (copied from host memory)."""
+
+    def __init__(self, off=None, col=None, *, n_cap: int | None = None, nnz_cap: int | None = None,
+                 validate: bool = False, stream=None):
+        torch = _require_cuda()
+        self._lib = load_library()
+        self._h = _P()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        if off is not None:
+            n = len(off) - 1
+            nnz = len(col)
+            n_cap = max(n, n_cap or 0)
+            nnz_cap = max(nnz, nnz_cap or 0)
+        check(self._lib.tec_graph_create(int(n_cap or 0), int(nnz_cap or 0), _P(stream.cuda_stream),
+                                         ctypes.byref(self._h)))
+        self.n = 0
+        self.m = 0
+        if off is not None:
+            self.load(off, col, validate=validate)
+
+    # ------------------------------------------------------------ lifetime
+    def load(self, off, col, validate: bool = False):
+        host = isinstance(off, np.ndarray)
+        flags = (HOST_PTR if host else 0) | (VALIDATE if validate else 0)
+        if host:
+            off = np.ascontiguousarray(off)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            i64 = off.dtype == np.int64
+            if not i64:
+                off = off.astype(np.int32)
+        else:
+            i64 = off.dtype == _torch().int64
+            off = off.contiguous()
+            col = col.contiguous()
+        self._keep = (off, col)
+        check(self._lib.tec_graph_load(self._h, _ptr(off), int(i64), _ptr(col), len(off) - 1, len(col), flags))
+        self._keep = None
+        n, m = ctypes.c_int64(), ctypes.c_int64()
+        check(self._lib.tec_graph_info(self._h, ctypes.byref(n), ctypes.byref(m)))
+        self.n, self.m = n.value, m.value
+        return self
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            check(self._lib.tec_graph_free(self._h))
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def sync(self):
+        check(self._lib.tec_sync(self._h))
+
+    def set_stage_events(self, events):
+        """torch.cuda.Event objects (timing enabled) recorded between the fused pass's stages."""
+        self._events = list(events)
+        for e in self._events:
+            if not e.cuda_event:          # torch creates its events lazily on first record
+                e.record(self.stream)
+        arr = (_P * 5)(*[_P(e.cuda_event) for e in self._events])
+        check(self._lib.tec_set_stage_events(self._h, arr, len(self._events)))
+
+    # ------------------------------------------------------------ steps
+    def _empty(self, count, dtype):
+        torch = _torch()
+        return torch.empty(max(count, 0), dtype=dtype, device="cuda")
+
+    def orient(self):
+        check(self._lib.tec_orient(self._h))
+
+    def support(self):
+        check(self._lib.tec_support(self._h))
+
+    def oriented_csr(self):
+        torch = _torch()
+        ooff = self._empty(self.n + 1, torch.int64)
+        ocol = self._empty(self.m, torch.int32)
+        check(self._lib.tec_oriented_csr(self._h, _ptr(ooff), _ptr(ocol)))
+        return ooff, ocol
+
+    def edge_list(self):
+        torch = _torch()
+        u = self._empty(self.m, torch.int32)
+        v = self._empty(self.m, torch.int32)
+        check(self._lib.tec_edge_list(self._h, _ptr(u), _ptr(v)))
+        return u, v
+
+    def edge_support(self, wedges: bool = True):
+        """(t, wedge) in canonical order, uint32 values in int32 tensors."""
+        torch = _torch()
+        t = self._empty(self.m, torch.int32)
+        w = self._empty(self.m, torch.int32) if wedges else None
+        check(self._lib.tec_edge_support(self._h, _ptr(t), _ptr(w)))
+        return t, w
+
+    def edge_weights(self, measure: int = TECTONIC):
+        torch = _torch()
+        w = self._empty(self.m, torch.float64)
+        check(self._lib.tec_edge_weights(self._h, int(measure), _ptr(w)))
+        return w
+
+    def prune(self, measure: int, p: int, q: int, mask: bool = False, count: bool = True):
+        torch = _torch()
+        keep = self._empty(self.m, torch.uint8) if mask else None
+        kept = ctypes.c_int64(-1)
+        check(self._lib.tec_prune(self._h, int(measure), int(p), int(q), _ptr(keep),
+                                  ctypes.byref(kept) if count else None))
+        return keep, (kept.value if count else None)
+
+    def components(self, labels=None, count: bool = True):
+        torch = _torch()
+        if labels is None:
+            labels = self._empty(self.n, torch.int32)
+        nc = ctypes.c_int64(-1)
+        check(self._lib.tec_components(self._h, _ptr(labels), ctypes.byref(nc) if count else None))
+        return labels, (nc.value if count else None)
+
+    def full_pass(self, measure: int, p: int, q: int, labels=None, count: bool = True):
+        torch = _torch()
+        if labels is None:
+            labels = self._empty(self.n, torch.int32)
+        nc = ctypes.c_int64(-1)
+        check(self._lib.tec_full_pass(self._h, int(measure), int(p), int(q), _ptr(labels),
+                                      ctypes.byref(nc) if count else None))
+        return labels, (nc.value if count else None)
+
+    def full_pass_host(self, off: np.ndarray, col: np.ndarray, measure: int, p: int, q: int,
+                       labels: np.ndarray | None = None):
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        n = len(off) - 1
+        if labels is None:
+            labels = np.empty(n, dtype=np.int32)
+        nc = ctypes.c_int64(-1)
+        check(self._lib.tec_full_pass_host(self._h, _ptr(off), _ptr(col), n, len(col), int(measure), int(p),
+                                           int(q), _ptr(labels), ctypes.byref(nc)))
+        n_, m_ = ctypes.c_int64(), ctypes.c_int64()
+        check(self._lib.tec_graph_info(self._h, ctypes.byref(n_), ctypes.byref(m_)))
+        self.n, self.m = n_.value, m_.value
+        return labels, nc.value

@@ -1,0 +1,62 @@
+"""C-ABI library checks that need no GPU: it loads, exports every symbol the
+public header declares, and the binding refuses to run without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2412_12382_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tectonic.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tec_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = libbuild.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("tec_graph_upload", "tec_edge_support", "tec_edge_weights", "tec_prune",
+              "tec_components", "tec_full_pass", "tec_full_pass_host"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_version_and_error_buffer(lib):
+    lib.tec_version.restype = ctypes.c_int
+    assert lib.tec_version() == 100
+    lib.tec_last_error.restype = ctypes.c_size_t
+    lib.tec_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    assert lib.tec_last_error(None, 0) >= 0
+
+
+def test_null_arguments_rejected_without_touching_a_device(lib):
+    from paper_2412_12382_gb300 import tectonic as T
+    L = T.load_library()
+    assert L.tec_graph_free(None) == 0
+    assert L.tec_graph_info(None, None, None) == 1          # TEC_EINVAL
+    assert L.tec_prune(None, 0, 1, 10, None, None) == 1
+    assert L.tec_graph_create(-1, 0, None, None) == 1
+
+
+def test_binding_fails_loudly_without_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2412_12382_gb300 import Graph
+    with pytest.raises(RuntimeError):
+        Graph(n_cap=4, nnz_cap=8)

@@ -60,8 +60,8 @@ tec_status dalloc(T **p, int64_t count, const char *what) {
 }
 
 void free_graph_memory(tec_graph *g) {
-    void *ptrs[] = {g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->parent, g->vlist,
-                    g->flags, g->tile_cnt, g->tile_base, g->bsum, g->uoff, g->ucnt, g->ctr};
+    void *ptrs[] = {g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->parent, g->tasks,
+                    g->flags, g->tile_cnt, g->tile_base, g->bsum, g->uoff, g->ucnt, g->labels, g->ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (g->ctr_host) cudaFreeHost(g->ctr_host);
@@ -103,7 +103,8 @@ tec_status ensure_oriented(tec_graph *g) {
 tec_status ensure_support(tec_graph *g) {
     TEC_TRY(ensure_oriented(g));
     if (g->supported) return TEC_OK;
-    TEC_CUDA(launch_support(g->ooff, g->ocol, g->n, g->m, g->t, g->vlist, g->ctr, g->num_sms, g->stream));
+    TEC_CUDA(launch_support(g->off, g->col, g->flags, g->ooff, g->ocol, g->n, g->m, g->t, g->tasks, g->task_cap,
+                            g->ctr, g->num_sms, g->stream));
     g->supported = true;
     g->pruned = g->hooked = false;
     return TEC_OK;
@@ -203,7 +204,8 @@ tec_status tec_graph_create(int64_t n_cap, int64_t nnz_cap, void *stream, tec_gr
     if (s == TEC_OK) s = dalloc(&g->t, g->m_cap, "triangle counts");
     if (s == TEC_OK) s = dalloc(&g->keep, mwords, "keep mask");
     if (s == TEC_OK) s = dalloc(&g->parent, n_cap, "union-find parents");
-    if (s == TEC_OK) s = dalloc(&g->vlist, n_cap, "vertex work list");
+    g->task_cap = support_task_capacity(n_cap, nnz_cap);
+    if (s == TEC_OK) s = dalloc(&g->tasks, g->task_cap, "support task list");
     if (s == TEC_OK) s = dalloc(&g->flags, ntiles * (TILE / 32), "orientation bits");
     if (s == TEC_OK) s = dalloc(&g->tile_cnt, ntiles + 1, "tile counts");
     if (s == TEC_OK) s = dalloc(&g->tile_base, ntiles + 1, "tile offsets");
@@ -450,9 +452,12 @@ tec_status tec_full_pass_host(tec_graph *g, const int64_t *row_off_host, const i
     TEC_TRY(check_threshold((int)measure, p, q));
     DeviceGuard dg(g->device);
     TEC_TRY(tec_graph_load(g, row_off_host, 1, col_host, n, nnz, TEC_HOST_PTR));
-    TEC_TRY(run_full_pass(g, (int)measure, p, q, g->parent));
+    // Labels need their own buffer: while the finishing kernel resolves roots,
+    // path compression may still re-point parent[x] at an intermediate ancestor.
+    if (!g->labels) TEC_TRY(dalloc(&g->labels, g->n_cap, "label buffer"));
+    TEC_TRY(run_full_pass(g, (int)measure, p, q, g->labels));
     if (n > 0)
-        TEC_CUDA(cudaMemcpyAsync(labels_host, g->parent, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost,
+        TEC_CUDA(cudaMemcpyAsync(labels_host, g->labels, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost,
                                  g->stream));
     TEC_TRY(read_counters(g));
     if (ncomp_out) *ncomp_out = (int64_t)g->ctr_host[C_NCOMP];

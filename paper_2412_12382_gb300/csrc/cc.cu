@@ -33,6 +33,8 @@ k_cc_hook(const int64_t *ooff, const int32_t *ocol, const uint32_t *keep, int64_
     }
 }
 
+// labels must not alias parent: other threads' path compression can still
+// re-point parent[x] at an intermediate ancestor after x has been resolved.
 __global__ void k_cc_finish(int32_t *parent, int64_t n, int32_t *labels, unsigned long long *ctr) {
     int roots = 0;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;

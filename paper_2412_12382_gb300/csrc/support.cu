@@ -1,19 +1,33 @@
 // Per-edge triangle counts t(u,v) = |N(u) n N(v)| (Sec. I) on the oriented CSR.
 //
-// Every triangle {u, v, w} with (deg, id)-rank u < v < w is listed exactly once,
-// from u: v runs over N+(u) and w over N+(v) n N+(u).  It is credited to its
-// three edges: u->v and u->w live in row u (accumulated by the owning warp or
-// block in shared memory, one global add per edge), v->w lives in row v (one
-// global atomic add per triangle).  Integer sums do not depend on the order of
-// the adds, so the counts are exact and deterministic.
+// Every triangle {a, b, c} with (deg, id)-rank a < b < c is found exactly once,
+// as the element c of N+(a) n N+(b) for the oriented edge a -> b, and is
+// credited to its three oriented edges a->b, a->c, b->c.  Integer sums do not
+// depend on the order of the adds, so the counts are exact and deterministic.
 //
-// Work is binned by out-degree d+(u):
-//   d+(u) <= 32   one warp per u, N+(u) held one id per lane, membership of
-//                 each w by a 5-step lane-shuffle binary search;
-//   d+(u) >  32   one block per u, N+(u) staged in shared memory in chunks of
-//                 8192 ids, membership by binary search in shared memory,
-//                 blocks take vertices from a global work counter.
-// Reads of N+(v) are coalesced: a warp reads consecutive ids of one row.
+// Each oriented edge x -> y is intersected from the side with the shorter
+// out-row, so the probe work is the sum over edges of min(d+(x), d+(y)):
+//   U-mode, centre c = x, when d+(y) <= d+(x): the ids of N+(y) are probed
+//     against the staged set N+(c);
+//   V-mode, centre c = y, when d+(x) <  d+(y): the ids of N+(x) are probed
+//     against the staged set N+(c).  The in-neighbours x of c are the entries
+//     of c's symmetric row whose orientation bit is clear, so no transposed
+//     graph is needed.
+// A probe row is never longer than the staged set.
+//
+// The candidates of centre c are indexed 0 .. d+(c) + deg(c) - 1: first the
+// U-mode candidates N+(c), then the entries of c's symmetric row (V-mode).  A
+// visit is a contiguous slice of them, sized for about 2^20 probes:
+//   d+(c) <= 256  warp visits: N+(c) staged in the warp's own slice of shared
+//                 memory (sorted ids plus a bitmap filter);
+//   d+(c) >  256  block visits: N+(c) staged per block in chunks of 4096 ids
+//                 (sorted ids plus a bitmap filter); the block's warps take
+//                 batches of candidates from a shared counter.
+// A warp handles 32 candidates at once: each lane loads one candidate's row
+// bounds (one round of latency for 32 rows), then the rows are read one after
+// another by the whole warp, coalesced, 128 ids per step.  One persistent
+// kernel (two blocks per SM) drains the block visits first, pulling them from
+// a global counter, then reuses the same shared memory for warp visits.
 #include <climits>
 
 #include "tec_internal.cuh"
@@ -22,180 +36,403 @@ namespace tec {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int SUP_THREADS = 256;
-constexpr int SUP_WARPS = SUP_THREADS / 32;
+constexpr int W_MAX = 256;                      // largest d+(c) of a warp visit
+constexpr int B_THREADS = 512;                  // block-visit kernel block
+constexpr int B_WARPS = B_THREADS / 32;
+constexpr int S_CHUNK = 4096;                   // staged ids per block chunk
+constexpr int64_t VISIT_PROBES = 1 << 20;       // target probes per visit
+constexpr int W_GRAB = 16;                      // warp visits taken per counter bump
+constexpr uint64_t VIS_MASK = (1ull << 32) - 1;
 
-__global__ void k_classify(const int64_t *ooff, int64_t n, int32_t *vlist, unsigned long long *ctr) {
-    if (graph_bad(ctr)) return;
-    const unsigned lane = lane_id();
-    const unsigned lt = (1u << lane) - 1u;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int64_t u = base + threadIdx.x;
-        const int64_t d = u < n ? ooff[u + 1] - ooff[u] : 0;
-        const bool small = d > 0 && d <= SMALL_ROW;
-        const bool large = d > SMALL_ROW;
-        const unsigned ms = __ballot_sync(FULL, small);
-        const unsigned ml = __ballot_sync(FULL, large);
-        unsigned long long bs = 0, bl = 0;
-        if (lane == 0) {
-            if (ms) bs = atomicAdd(&ctr[C_NSMALL], (unsigned long long)__popc(ms));
-            if (ml) bl = atomicAdd(&ctr[C_NLARGE], (unsigned long long)__popc(ml));
-        }
-        bs = __shfl_sync(FULL, bs, 0);
-        bl = __shfl_sync(FULL, bl, 0);
-        if (small) vlist[bs + __popc(ms & lt)] = (int32_t)u;
-        if (large) vlist[n - 1 - (int64_t)(bl + __popc(ml & lt))] = (int32_t)u;
-    }
-}
-
-__global__ void __launch_bounds__(SUP_THREADS)
-k_support_small(const int64_t *ooff, const int32_t *ocol, uint32_t *t, const int32_t *vlist,
-                const unsigned long long *ctr) {
-    __shared__ uint32_t s_cnt[SUP_WARPS][32];
-    if (graph_bad(ctr)) return;
-    const unsigned lane = lane_id();
-    const int w = threadIdx.x >> 5;
-    const int64_t nsmall = (int64_t)ctr[C_NSMALL];
-    for (int64_t it = (int64_t)blockIdx.x * SUP_WARPS + w; it < nsmall; it += (int64_t)gridDim.x * SUP_WARPS) {
-        const int32_t u = vlist[it];
-        const int64_t ub = ooff[u];
-        const int du = (int)(ooff[u + 1] - ub);
-        const int32_t a = (int)lane < du ? ocol[ub + lane] : INT_MAX;   // ascending over lanes
-        s_cnt[w][lane] = 0u;
-        __syncwarp();
-        for (int j = 0; j < du; ++j) {
-            const int32_t v = __shfl_sync(FULL, a, j);
-            const int64_t vb = ooff[v], ve = ooff[v + 1];
-            int hits = 0;
-            for (int64_t kb = vb; kb < ve; kb += 32) {
-                const int64_t k = kb + lane;
-                const int32_t x = k < ve ? ocol[k] : -1;
-                int p = 0;
-#pragma unroll
-                for (int st = 16; st >= 1; st >>= 1) {
-                    const int32_t c = __shfl_sync(FULL, a, p + st - 1);
-                    if (c < x) p += st;
-                }
-                const int32_t ap = __shfl_sync(FULL, a, p);
-                if (x >= 0 && ap == x) {
-                    ++hits;
-                    atomicAdd(&s_cnt[w][p], 1u);      // edge u -> x
-                    atomicAdd(&t[k], 1u);             // edge v -> x
-                }
-            }
-            hits = warp_sum(hits);
-            if (lane == 0 && hits) atomicAdd(&s_cnt[w][j], (uint32_t)hits);   // edge u -> v
-        }
-        __syncwarp();
-        if ((int)lane < du) {
-            const uint32_t c = s_cnt[w][lane];
-            if (c) atomicAdd(&t[ub + lane], c);
-        }
-        __syncwarp();
-    }
+__device__ __forceinline__ bool out_bit(const uint32_t *flags, int64_t e) {
+    return (flags[e >> 5] >> (e & 31)) & 1u;
 }
 
 __device__ __forceinline__ int64_t lower_bound_g(const int32_t *a, int64_t lo, int64_t hi, int32_t x) {
     while (lo < hi) {
-        int64_t mid = lo + (hi - lo) / 2;
+        const int64_t mid = lo + (hi - lo) / 2;
         if (a[mid] < x) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
 
-__global__ void __launch_bounds__(SUP_THREADS)
-k_support_large(const int64_t *ooff, const int32_t *ocol, int64_t n, uint32_t *t, const int32_t *vlist,
-                unsigned long long *ctr) {
-    extern __shared__ int32_t smem[];
-    int32_t *s_a = smem;
-    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + LARGE_CHUNK);
-    __shared__ long long s_item;
+// Candidates of one visit: du + deg candidates split into slices of vlen.
+__device__ __forceinline__ int64_t visit_len(int64_t du) {
+    int64_t v = VISIT_PROBES / (du > 0 ? du : 1);
+    return v < 256 ? 256 : (v > 65536 ? 65536 : v);
+}
+
+// One thread per vertex: emits the visits of centre c (warp list from the
+// front of tasks[], block list from the back).
+__global__ void k_make_visits(const int64_t *off, const int64_t *ooff, int64_t n, uint64_t *tasks, int64_t cap,
+                              unsigned long long *ctr) {
     if (graph_bad(ctr)) return;
     const unsigned lane = lane_id();
-    const int w = threadIdx.x >> 5;
-    const int64_t nlarge = (int64_t)ctr[C_NLARGE];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t c = base + threadIdx.x;
+        int64_t du = 0, deg = 0;
+        if (c < n) {
+            du = ooff[c + 1] - ooff[c];
+            deg = off[c + 1] - off[c];
+        }
+        // V-mode candidates exist only if c has in-neighbours
+        const int64_t ncand = du > 0 ? du + (deg > du ? deg : 0) : 0;
+        const int64_t cnt = ncand > 0 ? ceil_div(ncand, visit_len(du)) : 0;
+        const bool small = du <= W_MAX;
+        const int64_t my_w = small ? cnt : 0, my_b = small ? 0 : cnt;
+        int64_t sw = my_w, sb = my_b;          // inclusive warp scans
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t yw = __shfl_up_sync(FULL, sw, o), yb = __shfl_up_sync(FULL, sb, o);
+            if ((int)lane >= o) { sw += yw; sb += yb; }
+        }
+        unsigned long long bw = 0, bb = 0;
+        if (lane == 31) {
+            if (sw) bw = atomicAdd(&ctr[C_NWTASK], (unsigned long long)sw);
+            if (sb) bb = atomicAdd(&ctr[C_NBTASK], (unsigned long long)sb);
+        }
+        bw = __shfl_sync(FULL, bw, 31);
+        bb = __shfl_sync(FULL, bb, 31);
+        int64_t at = small ? (int64_t)bw + sw - my_w : (int64_t)bb + sb - my_b;
+        for (int64_t i = 0; i < cnt; ++i, ++at) {
+            const int64_t slot = small ? at : cap - 1 - at;
+            if (slot >= 0 && slot < cap) tasks[slot] = ((uint64_t)c << 32) | (uint64_t)i;
+            else flag_status(ctr, ST_BADGRAPH);
+        }
+    }
+}
+
+// Row bounds of candidate q of centre c (q < du: U-mode, else V-mode entry
+// off[c] + q - du).  len = 0 when the edge is not intersected from c.
+struct Cand {
+    int64_t rs;     // first probe position (in ocol)
+    int64_t jpos;   // V-mode with a chunked centre: position of c in N+(x), else -1
+    int len;
+    bool vmode;
+};
+
+__device__ __forceinline__ Cand load_cand(const int64_t *off, const int32_t *col, const uint32_t *flags,
+                                          const int64_t *ooff, const int32_t *ocol, int32_t c, int64_t cb,
+                                          int64_t du, int64_t q, bool chunked, int32_t lo_val, int32_t hi_val) {
+    Cand r{0, -1, 0, q >= du};
+    int32_t x = -1;
+    int64_t lim = du;
+    if (q < du) {
+        x = ocol[cb + q];
+    } else {
+        const int64_t e = off[c] + (q - du);
+        if (!out_bit(flags, e)) x = col[e];
+        lim = du - 1;
+    }
+    if (x < 0) return r;
+    int64_t rs = ooff[x], re = ooff[x + 1];
+    if (re - rs <= 0 || re - rs > lim) return r;
+    if (chunked) {
+        const int64_t r0 = rs, r1 = re;
+        rs = lower_bound_g(ocol, r0, r1, lo_val);
+        re = lower_bound_g(ocol, rs, r1, hi_val == INT_MAX ? hi_val : hi_val + 1);
+        if (r.vmode) r.jpos = lower_bound_g(ocol, r0, r1, c);
+    }
+    r.rs = rs;
+    r.len = (int)(re - rs);
+    return r;
+}
+
+// ------------------------------------------------------------------ membership
+//
+// The staged set S (sorted ids s_a[0..cl)) is tested through a one-hash
+// bitmap filter of 2^fb bits (fb chosen so that 2^fb >= 64 cl, so a miss is
+// a false positive with probability <= 1/64).  The filter test is loop-free;
+// the rare positives (true hits plus false positives) are pushed to a per-warp
+// queue and resolved 32 at a time by binary search in s_a, so the warp stays
+// converged on the hot path.
+
+constexpr int QCAP = 64;                 // per-warp queue of filter positives
+constexpr int UNROLL = 4;                // ids loaded per lane before the first is probed
+
+struct WarpScratch {
+    int32_t qw[QCAP];      // probed id
+    int32_t qs[QCAP];      // batch slot (candidate lane) of the probe row
+    int64_t qk[QCAP];      // position of the id in ocol
+    uint32_t rowhits[32];  // hits per candidate of the batch
+    int64_t jpos[32];      // V-mode: position of c in the candidate's row
+};
+
+__device__ __forceinline__ uint32_t fhash(int32_t w, int fb) {
+    return ((uint32_t)w * 0x9E3779B1u) >> (32 - fb);
+}
+
+__device__ __forceinline__ int filter_bits(int cl, int fb_max) {
+    int fb = 10;
+    while (fb < fb_max && (1 << fb) < 64 * cl) ++fb;
+    return fb;
+}
+
+// Sets the filter bits of s_a[0..cl) (filter already cleared).
+__device__ __forceinline__ void build_filter(const int32_t *s_a, uint32_t *filt, int cl, int fb, int tid, int nthr) {
+    for (int i = tid; i < cl; i += nthr) {
+        const uint32_t h = fhash(s_a[i], fb);
+        atomicOr(&filt[h >> 5], 1u << (h & 31));
+    }
+}
+
+// Resolves queue entries [0, cnt) (cnt <= 32), one per lane.
+__device__ __forceinline__ void drain(WarpScratch &ws, int cnt, const int32_t *s_a, int cl, uint32_t *s_cnt,
+                                      uint32_t *t) {
+    const int lane = (int)lane_id();
+    if (lane < cnt) {
+        const int32_t w = ws.qw[lane];
+        int lo = 0, hi = cl;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_a[mid] < w) lo = mid + 1; else hi = mid;
+        }
+        if (lo < cl && s_a[lo] == w) {
+            atomicAdd(&s_cnt[lo], 1u);               // c -> w
+            atomicAdd(&t[ws.qk[lane]], 1u);          // x -> w
+            atomicAdd(&ws.rowhits[ws.qs[lane]], 1u);  // x -> c or c -> x, credited per row below
+        }
+    }
+    __syncwarp();
+}
+
+// One warp processes candidates q0 .. min(q0 + 32, qend) - 1 of centre c
+// against the staged chunk (s_a, cl, filter).  U-mode row hits are credited
+// to c -> x through s_cnt[q] when uv_local (the whole N+(c) is staged) or
+// through t otherwise; V-mode row hits to x -> c at the position of c in N+(x).
+__device__ __forceinline__ void process_batch(const int64_t *off, const int32_t *col, const uint32_t *flags,
+                                              const int64_t *ooff, const int32_t *ocol, uint32_t *t, int32_t c,
+                                              int64_t cb, int64_t du, int64_t q0, int64_t qend, bool chunked,
+                                              const int32_t *s_a, int cl, uint32_t *s_cnt, const uint32_t *filt,
+                                              int fb, bool uv_local, WarpScratch &ws, unsigned long long *ctr) {
+    const unsigned lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t q = q0 + lane;
+    Cand cd{0, -1, 0, false};
+    if (q < qend) cd = load_cand(off, col, flags, ooff, ocol, c, cb, du, q, chunked, s_a[0], s_a[cl - 1]);
+    ws.rowhits[lane] = 0u;
+    ws.jpos[lane] = cd.jpos;
+    __syncwarp();
+    unsigned todo = __ballot_sync(FULL, cd.len > 0);
+    int qn = 0;
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int64_t rs = __shfl_sync(FULL, cd.rs, src);
+        const int len = __shfl_sync(FULL, cd.len, src);
+        const bool vm = q0 + src >= du;
+        // UNROLL ids per lane per step: all loads are issued before any is used
+        for (int base = 0; base < len; base += 32 * UNROLL) {
+            int32_t w[UNROLL];
+#pragma unroll
+            for (int j = 0; j < UNROLL; ++j) {
+                const int i = base + 32 * j + (int)lane;
+                w[j] = i < len ? __ldg(&ocol[rs + i]) : -1;
+            }
+#pragma unroll
+            for (int j = 0; j < UNROLL; ++j) {
+                const int i = base + 32 * j + (int)lane;
+                bool pos = false;
+                if (w[j] >= 0) {
+                    if (vm && w[j] == c) ws.jpos[src] = rs + i;
+                    const uint32_t h = fhash(w[j], fb);
+                    pos = (filt[h >> 5] >> (h & 31)) & 1u;
+                }
+                const unsigned pm = __ballot_sync(FULL, pos);
+                if (pos) {
+                    const int slot = qn + __popc(pm & lt);
+                    ws.qw[slot] = w[j];
+                    ws.qk[slot] = rs + i;
+                    ws.qs[slot] = src;
+                }
+                qn += __popc(pm);
+                if (qn >= 32) {
+                    __syncwarp();
+                    drain(ws, 32, s_a, cl, s_cnt, t);
+                    if ((int)lane < qn - 32) {
+                        ws.qw[lane] = ws.qw[32 + lane];
+                        ws.qk[lane] = ws.qk[32 + lane];
+                        ws.qs[lane] = ws.qs[32 + lane];
+                    }
+                    qn -= 32;
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (qn) drain(ws, qn, s_a, cl, s_cnt, t);
+    const uint32_t hits = ws.rowhits[lane];
+    if (hits) {
+        if (q < du) {
+            if (uv_local) atomicAdd(&s_cnt[q], hits);       // c -> x (whole N+(c) staged)
+            else atomicAdd(&t[cb + q], hits);               // c -> x
+        } else {
+            const int64_t jp = ws.jpos[lane];
+            if (jp >= 0) atomicAdd(&t[jp], hits);           // x -> c
+            else flag_status(ctr, ST_BADGRAPH);
+        }
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ warp visits
+
+constexpr int W_FB = 14;                             // warp filter: 2^14 bits = 2 KB
+constexpr int W_SLICE = (1 << W_FB) / 32 + 2 * W_MAX; // words per warp: filter, s_a, s_cnt
+
+// One warp, one visit of a centre with d+(c) <= W_MAX, on the warp's own
+// slice of shared memory.
+__device__ __forceinline__ void warp_visit(const int64_t *off, const int32_t *col, const uint32_t *flags,
+                                           const int64_t *ooff, const int32_t *ocol, uint32_t *t, uint64_t task,
+                                           int32_t *slice, WarpScratch &ws, unsigned long long *ctr) {
+    const unsigned lane = lane_id();
+    uint32_t *filt = reinterpret_cast<uint32_t *>(slice);
+    int32_t *s_a = slice + (1 << W_FB) / 32;
+    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(s_a + W_MAX);
+    const int32_t c = (int32_t)(task >> 32);
+    const int64_t vis = (int64_t)(task & VIS_MASK);
+    const int64_t cb = ooff[c];
+    const int du = (int)(ooff[c + 1] - cb);
+    const int64_t deg = off[c + 1] - off[c];
+    const int64_t ncand = du + (deg > du ? deg : 0);
+    const int64_t vl = visit_len(du);
+    const int64_t qbeg = vis * vl, qend = min(ncand, qbeg + vl);
+    const int fb = filter_bits(du, W_FB);
+    for (int i = (int)lane; i < (1 << fb) / 32; i += 32) filt[i] = 0u;
+    for (int i = (int)lane; i < du; i += 32) {
+        s_a[i] = ocol[cb + i];
+        s_cnt[i] = 0u;
+    }
+    __syncwarp();
+    build_filter(s_a, filt, du, fb, (int)lane, 32);
+    __syncwarp();
+    for (int64_t q0 = qbeg; q0 < qend; q0 += 32)
+        process_batch(off, col, flags, ooff, ocol, t, c, cb, du, q0, qend, false, s_a, du, s_cnt, filt, fb, true,
+                      ws, ctr);
+    __syncwarp();
+    for (int i = (int)lane; i < du; i += 32) {
+        const uint32_t cv = s_cnt[i];
+        if (cv) atomicAdd(&t[cb + i], cv);
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ block visits
+
+constexpr int B_FB = 18;                             // block filter: 2^18 bits = 32 KB
+constexpr int B_WORDS = (1 << B_FB) / 32 + 2 * S_CHUNK;
+static_assert(B_WARPS * W_SLICE <= B_WORDS, "warp slices must fit the block buffer");
+
+// Persistent kernel: every block first drains the block-visit list (pulled
+// from a global counter, the block's warps taking batches of 32 candidates
+// from a shared counter), then its warps take warp visits in groups of W_GRAB.
+__global__ void __launch_bounds__(B_THREADS, 2)
+k_support(const int64_t *off, const int32_t *col, const uint32_t *flags, const int64_t *ooff,
+          const int32_t *ocol, uint32_t *t, const uint64_t *tasks, int64_t cap, unsigned long long *ctr) {
+    extern __shared__ int32_t smem[];
+    uint32_t *filt = reinterpret_cast<uint32_t *>(smem);              // 2^B_FB bits
+    int32_t *s_a = smem + (1 << B_FB) / 32;                           // S_CHUNK ids
+    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(s_a + S_CHUNK);      // S_CHUNK counters
+    __shared__ WarpScratch s_ws[B_WARPS];
+    __shared__ long long s_item;
+    __shared__ int s_next;
+    if (graph_bad(ctr)) return;
+    const unsigned lane = lane_id();
+    const int wi = threadIdx.x >> 5;
+    WarpScratch &ws = s_ws[wi];
+    const int64_t ntasks = (int64_t)ctr[C_NBTASK];
     for (;;) {
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(&ctr[C_NEXT], 1ull);
         __syncthreads();
         const int64_t it = s_item;
         __syncthreads();
-        if (it >= nlarge) break;
-        const int32_t u = vlist[n - 1 - it];
-        const int64_t ub = ooff[u];
-        const int64_t du = ooff[u + 1] - ub;
-        const bool chunked = du > LARGE_CHUNK;
-        for (int64_t c0 = 0; c0 < du; c0 += LARGE_CHUNK) {
-            const int cl = (int)(du - c0 < LARGE_CHUNK ? du - c0 : LARGE_CHUNK);
-            for (int i = threadIdx.x; i < cl; i += SUP_THREADS) {
-                s_a[i] = ocol[ub + c0 + i];
+        if (it >= ntasks) break;
+        const uint64_t task = tasks[cap - 1 - it];
+        const int32_t c = (int32_t)(task >> 32);
+        const int64_t vis = (int64_t)(task & VIS_MASK);
+        const int64_t cb = ooff[c];
+        const int64_t du = ooff[c + 1] - cb;
+        const int64_t deg = off[c + 1] - off[c];
+        const int64_t ncand = du + (deg > du ? deg : 0);
+        const int64_t vl = visit_len(du);
+        const int64_t qbeg = vis * vl, qend = min(ncand, qbeg + vl);
+        const bool chunked = du > S_CHUNK;
+        for (int64_t c0 = 0; c0 < du; c0 += S_CHUNK) {
+            const int cl = (int)min((int64_t)S_CHUNK, du - c0);
+            const int fb = filter_bits(cl, B_FB);
+            for (int i = threadIdx.x; i < (1 << fb) / 32; i += B_THREADS) filt[i] = 0u;
+            for (int i = threadIdx.x; i < cl; i += B_THREADS) {
+                s_a[i] = ocol[cb + c0 + i];
                 s_cnt[i] = 0u;
             }
+            if (threadIdx.x == 0) s_next = 0;
             __syncthreads();
-            const int32_t lo_val = s_a[0], hi_val = s_a[cl - 1];
-            for (int64_t j = w; j < du; j += SUP_WARPS) {
-                const int32_t v = ocol[ub + j];
-                int64_t vb = ooff[v], ve = ooff[v + 1];
-                if (chunked) {
-                    vb = lower_bound_g(ocol, vb, ve, lo_val);
-                    ve = lower_bound_g(ocol, vb, ve, hi_val == INT_MAX ? hi_val : hi_val + 1);
-                }
-                int hits = 0;
-                for (int64_t k = vb + lane; k < ve; k += 32) {
-                    const int32_t x = ocol[k];
-                    int lo = 0, hi = cl;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (s_a[mid] < x) lo = mid + 1; else hi = mid;
-                    }
-                    if (lo < cl && s_a[lo] == x) {
-                        ++hits;
-                        atomicAdd(&s_cnt[lo], 1u);     // edge u -> x
-                        atomicAdd(&t[k], 1u);          // edge v -> x
-                    }
-                }
-                hits = warp_sum(hits);
-                if (lane == 0 && hits) atomicAdd(&t[ub + j], (uint32_t)hits);   // edge u -> v
+            build_filter(s_a, filt, cl, fb, threadIdx.x, B_THREADS);
+            __syncthreads();
+            for (;;) {
+                int b = 0;
+                if (lane == 0) b = atomicAdd(&s_next, 32);
+                b = __shfl_sync(FULL, b, 0);
+                if (qbeg + b >= qend) break;
+                process_batch(off, col, flags, ooff, ocol, t, c, cb, du, qbeg + b, qend, chunked, s_a, cl, s_cnt,
+                              filt, fb, false, ws, ctr);
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < cl; i += SUP_THREADS) {
-                const uint32_t c = s_cnt[i];
-                if (c) atomicAdd(&t[ub + c0 + i], c);
+            for (int i = threadIdx.x; i < cl; i += B_THREADS) {
+                const uint32_t cv = s_cnt[i];
+                if (cv) atomicAdd(&t[cb + c0 + i], cv);
             }
             __syncthreads();
         }
     }
+    // phase 2: warp visits on per-warp slices of the same shared memory
+    int32_t *slice = smem + wi * W_SLICE;
+    const int64_t nw = (int64_t)ctr[C_NWTASK];
+    for (;;) {
+        unsigned long long g0 = 0;
+        if (lane == 0) g0 = atomicAdd(&ctr[C_NEXTW], (unsigned long long)W_GRAB);
+        g0 = __shfl_sync(FULL, g0, 0);
+        if ((int64_t)g0 >= nw) break;
+        const int64_t g1 = min(nw, (int64_t)g0 + W_GRAB);
+        for (int64_t it = (int64_t)g0; it < g1; ++it)
+            warp_visit(off, col, flags, ooff, ocol, t, tasks[it], slice, ws, ctr);
+    }
 }
 
 __global__ void k_reset_support_counters(unsigned long long *ctr) {
-    ctr[C_NSMALL] = 0;
-    ctr[C_NLARGE] = 0;
+    ctr[C_NWTASK] = 0;
+    ctr[C_NBTASK] = 0;
     ctr[C_NEXT] = 0;
+    ctr[C_NEXTW] = 0;
 }
 
 }  // namespace
 
-cudaError_t launch_support(const int64_t *ooff, const int32_t *ocol, int64_t n, int64_t m, uint32_t *t,
-                           int32_t *vlist, unsigned long long *ctr, int num_sms, cudaStream_t s) {
-    const int large_smem = 2 * LARGE_CHUNK * (int)sizeof(int32_t);
-    {
-        cudaError_t e = cudaFuncSetAttribute(k_support_large, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             large_smem);
-        if (e != cudaSuccess) return e;
-    }
+int64_t support_task_capacity(int64_t n, int64_t nnz) {
+    // per vertex at most ceil((d+ + deg) / 256) <= 1 + (d+ + deg) / 256 visits
+    return n + (nnz + nnz / 2) / 256 + 64;
+}
+
+cudaError_t launch_support(const int64_t *off, const int32_t *col, const uint32_t *flags, const int64_t *ooff,
+                           const int32_t *ocol, int64_t n, int64_t m, uint32_t *t, uint64_t *tasks,
+                           int64_t task_cap, unsigned long long *ctr, int num_sms, cudaStream_t s) {
     if (m > 0) {
         cudaError_t e = cudaMemsetAsync(t, 0, (size_t)m * sizeof(uint32_t), s);
         if (e != cudaSuccess) return e;
     }
     if (n <= 0 || m <= 0) return cudaSuccess;
+    const int bsmem = B_WORDS * (int)sizeof(int32_t);
+    cudaError_t e = cudaFuncSetAttribute(k_support, cudaFuncAttributeMaxDynamicSharedMemorySize, bsmem);
+    if (e != cudaSuccess) return e;
     k_reset_support_counters<<<1, 1, 0, s>>>(ctr);
     {
-        int64_t g = ceil_div(n, 256);
-        k_classify<<<(unsigned)(g < 65536 ? g : 65536), 256, 0, s>>>(ooff, n, vlist, ctr);
+        const int64_t g = ceil_div(n, 256);
+        k_make_visits<<<(unsigned)(g < 65536 ? g : 65536), 256, 0, s>>>(off, ooff, n, tasks, task_cap, ctr);
     }
-    k_support_small<<<(unsigned)(num_sms * 8), SUP_THREADS, 0, s>>>(ooff, ocol, t, vlist, ctr);
-    k_support_large<<<(unsigned)(num_sms * 2), SUP_THREADS, large_smem, s>>>(ooff, ocol, n, t, vlist, ctr);
-    count_launches(4);
+    k_support<<<(unsigned)(num_sms * 2), B_THREADS, bsmem, s>>>(off, col, flags, ooff, ocol, t, tasks, task_cap, ctr);
+    count_launches(3);
     return cudaGetLastError();
 }
 

@@ -29,9 +29,10 @@ enum Ctr : int {
     C_STATUS = 0,
     C_KEPT = 1,
     C_NCOMP = 2,
-    C_NSMALL = 3,
-    C_NLARGE = 4,
+    C_NWTASK = 3,
+    C_NBTASK = 4,
     C_NEXT = 5,
+    C_NEXTW = 6,
     C_COUNT = 16
 };
 
@@ -40,11 +41,11 @@ constexpr int TILE_THREADS = 256;
 constexpr int TILE_ITEMS = 8;
 constexpr int TILE = TILE_THREADS * TILE_ITEMS;   // 2048 entries, a multiple of 32
 
-// Rows with at most this many oriented neighbours are handled by one warp in
-// the support kernel; larger rows get a whole block.
+// Centres with at most this many oriented neighbours are handled by one warp
+// in the support kernels; larger ones by a whole block.
 constexpr int SMALL_ROW = 32;
-// Oriented neighbours of one large row staged per shared-memory chunk.
-constexpr int LARGE_CHUNK = 8192;
+// Candidates (probe rows) per support task.
+constexpr int64_t TASK_C = 256;
 
 // Retry cap of one union-find link (each retry strictly lowers a root id, so a
 // correct run never needs more than n).
@@ -70,7 +71,7 @@ void count_launches(int k);
         if (s_ != TEC_OK) return s_;                                                          \
     } while (0)
 
-inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // ---------------------------------------------------------------- launchers
 // Each returns cudaGetLastError() of its launches; all run on `s`.
@@ -93,10 +94,13 @@ cudaError_t launch_orient(const int64_t *off, const int32_t *col, const int32_t 
                           int64_t *bsum, int64_t *ooff, int32_t *ocol, int64_t m,
                           unsigned long long *ctr, cudaStream_t s);
 
-// support.cu: t[j] for every oriented edge (t must be zeroed first; done inside).
-cudaError_t launch_support(const int64_t *ooff, const int32_t *ocol, int64_t n, int64_t m,
-                           uint32_t *t, int32_t *vlist, unsigned long long *ctr, int num_sms,
-                           cudaStream_t s);
+// support.cu: t[j] for every oriented edge (zeroed inside).  `flags` are the
+// orientation bits of the symmetric entries; `tasks` holds task_cap entries.
+int64_t support_task_capacity(int64_t n, int64_t nnz);
+cudaError_t launch_support(const int64_t *off, const int32_t *col, const uint32_t *flags,
+                           const int64_t *ooff, const int32_t *ocol, int64_t n, int64_t m,
+                           uint32_t *t, uint64_t *tasks, int64_t task_cap,
+                           unsigned long long *ctr, int num_sms, cudaStream_t s);
 
 // prune.cu
 struct PruneArgs {
@@ -174,13 +178,15 @@ struct tec_graph {
     uint32_t *t = nullptr;
     uint32_t *keep = nullptr;
     int32_t *parent = nullptr;
-    int32_t *vlist = nullptr;
+    uint64_t *tasks = nullptr;      // support work list
+    int64_t task_cap = 0;
     uint32_t *flags = nullptr;
     int64_t *tile_cnt = nullptr;
     int64_t *tile_base = nullptr;
     int64_t *bsum = nullptr;
     int64_t *uoff = nullptr;        // export only, allocated on first export
     int32_t *ucnt = nullptr;        // export only
+    int32_t *labels = nullptr;      // host-buffer pass only, allocated on first use
     unsigned long long *ctr = nullptr;      // device counter block
     unsigned long long *ctr_host = nullptr; // pinned mirror for reads
 

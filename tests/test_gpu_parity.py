@@ -211,3 +211,23 @@ def test_rmat20_config_full_parity(tec):
     off, col = goff.cpu().numpy(), gcol.cpu().numpy()
     del goff, gcol
     check_all(tec, off, col, [(O.TECTONIC, 1, 10), (O.TW, 1, 10)])
+
+
+def test_repeated_runs_are_identical(tec):
+    # atomics and lock-free union-find run in a different order every time; the
+    # exact results must not: 40 runs of every path against the oracle
+    import torch
+    off, col, _ = planted_partition(4, 500, 0.05, 0.002, seed=1)
+    ref = O.full_pass(off, col, O.TECTONIC, 3, 50)
+    g = _gpu_graph(tec, off, col)
+    g2 = tec.Graph(n_cap=len(off) - 1, nnz_cap=len(col))
+    for _ in range(40):
+        g.support()
+        t, _ = g.edge_support(wedges=False)
+        assert np.array_equal(_u32(t), ref.t)
+        lab, nc = g.full_pass(tec.TECTONIC, 3, 50)
+        assert nc == ref.ncomp and np.array_equal(lab.cpu().numpy(), ref.labels)
+        hl, hnc = g2.full_pass_host(off, col, tec.TECTONIC, 3, 50)
+        assert hnc == ref.ncomp and np.array_equal(hl, ref.labels)
+    g.free()
+    g2.free()

@@ -19,15 +19,16 @@
 // U-mode candidates N+(c), then the entries of c's symmetric row (V-mode).  A
 // visit is a contiguous slice of them, sized for about 2^20 probes:
 //   d+(c) <= 256  warp visits: N+(c) staged in the warp's own slice of shared
-//                 memory (sorted ids plus a bitmap filter);
+//                 memory (sorted ids, bitmap filter, bucket directory);
 //   d+(c) >  256  block visits: N+(c) staged per block in chunks of 4096 ids
-//                 (sorted ids plus a bitmap filter); the block's warps take
-//                 batches of candidates from a shared counter.
+//                 (sorted ids, bitmap filter, bucket directory); the block's
+//                 warps take batches of candidates from a shared counter.
 // A warp handles 32 candidates at once: each lane loads one candidate's row
-// bounds (one round of latency for 32 rows), then the rows are read one after
-// another by the whole warp, coalesced, 128 ids per step.  One persistent
-// kernel (two blocks per SM) drains the block visits first, pulling them from
-// a global counter, then reuses the same shared memory for warp visits.
+// bounds (one round of latency for 32 rows); long rows are then read one after
+// another by the whole warp, coalesced, 128 ids per step, and short rows are
+// packed end to end over the lanes.  One persistent kernel (two blocks per SM)
+// drains the block visits first, pulling them from a global counter, then
+// reuses the same shared memory for warp visits.
 #include <climits>
 
 #include "tec_internal.cuh"
@@ -141,22 +142,38 @@ __device__ __forceinline__ Cand load_cand(const int64_t *off, const int32_t *col
 
 // ------------------------------------------------------------------ membership
 //
-// The staged set S (sorted ids s_a[0..cl)) is tested through a one-hash
-// bitmap filter of 2^fb bits (fb chosen so that 2^fb >= 64 cl, so a miss is
+// The staged set S (sorted ids a[0..cl)) is tested through a one-hash bitmap
+// filter of 2^fb bits (2^fb >= 64 cl where shared memory allows, so a miss is
 // a false positive with probability <= 1/64).  The filter test is loop-free;
-// the rare positives (true hits plus false positives) are pushed to a per-warp
-// queue and resolved 32 at a time by binary search in s_a, so the warp stays
-// converged on the hot path.
+// the positives (triangles plus false positives) are pushed to a per-warp
+// queue and resolved 32 at a time through a bucket directory over S: bucket
+// b = (id >> shift) - base holds the positions dir[b] .. dir[b+1]-1 of its ids
+// in a, about one id per bucket, so a lookup is two shared loads and a short
+// scan.
 
 constexpr int QCAP = 64;                 // per-warp queue of filter positives
 constexpr int UNROLL = 4;                // ids loaded per lane before the first is probed
+constexpr int SHORT_ROW = 96;            // rows up to this length are packed across lanes
 
 struct WarpScratch {
+    int64_t qk[QCAP];      // position of the probed id in ocol
     int32_t qw[QCAP];      // probed id
     int32_t qs[QCAP];      // batch slot (candidate lane) of the probe row
-    int64_t qk[QCAP];      // position of the id in ocol
     uint32_t rowhits[32];  // hits per candidate of the batch
     int64_t jpos[32];      // V-mode: position of c in the candidate's row
+};
+
+// One staged chunk of N+(c) with its filter and directory (shared memory).
+struct Staged {
+    const int32_t *a;      // sorted ids
+    int cl;                // number of ids
+    uint32_t *cnt;         // per-id triangle counters (edge c -> a[i])
+    const uint32_t *filt;  // 2^fb-bit filter
+    int fb;
+    const uint16_t *dir;   // nb + 1 bucket starts
+    int shift;
+    int32_t base;
+    int nb;
 };
 
 __device__ __forceinline__ uint32_t fhash(int32_t w, int fb) {
@@ -169,104 +186,164 @@ __device__ __forceinline__ int filter_bits(int cl, int fb_max) {
     return fb;
 }
 
-// Sets the filter bits of s_a[0..cl) (filter already cleared).
-__device__ __forceinline__ void build_filter(const int32_t *s_a, uint32_t *filt, int cl, int fb, int tid, int nthr) {
-    for (int i = tid; i < cl; i += nthr) {
-        const uint32_t h = fhash(s_a[i], fb);
+// Stages a[0..cl) (already in shared memory) into filter and directory with
+// threads tid, tid + nthr, ...; the caller clears the filter first and
+// synchronises before and after.
+__device__ __forceinline__ void index_staged(Staged &S, uint32_t *filt, uint16_t *dir, int nb_max, int tid,
+                                             int nthr) {
+    const int32_t lo = S.a[0], hi = S.a[S.cl - 1];
+    int sh = 0;
+    while (((hi >> sh) - (lo >> sh)) >= nb_max) ++sh;
+    S.shift = sh;
+    S.base = lo >> sh;
+    S.nb = (hi >> sh) - S.base + 1;
+    for (int i = tid; i < S.cl; i += nthr) {
+        const int32_t v = S.a[i];
+        const uint32_t h = fhash(v, S.fb);
         atomicOr(&filt[h >> 5], 1u << (h & 31));
+        const int b = (v >> sh) - S.base;
+        const int bp = i == 0 ? -1 : (S.a[i - 1] >> sh) - S.base;
+        for (int x = bp + 1; x <= b; ++x) dir[x] = (uint16_t)i;
+        if (i == S.cl - 1)
+            for (int x = b + 1; x <= S.nb; ++x) dir[x] = (uint16_t)S.cl;
     }
 }
 
+// Position of w in S.a, or -1.
+__device__ __forceinline__ int staged_find(const Staged &S, int32_t w) {
+    const int b = (w >> S.shift) - S.base;
+    if (b < 0 || b >= S.nb) return -1;
+    for (int i = S.dir[b], e = S.dir[b + 1]; i < e; ++i) {
+        const int32_t v = S.a[i];
+        if (v >= w) return v == w ? i : -1;
+    }
+    return -1;
+}
+
 // Resolves queue entries [0, cnt) (cnt <= 32), one per lane.
-__device__ __forceinline__ void drain(WarpScratch &ws, int cnt, const int32_t *s_a, int cl, uint32_t *s_cnt,
-                                      uint32_t *t) {
+__device__ __forceinline__ void drain(WarpScratch &ws, int cnt, const Staged &S, uint32_t *t) {
     const int lane = (int)lane_id();
     if (lane < cnt) {
-        const int32_t w = ws.qw[lane];
-        int lo = 0, hi = cl;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (s_a[mid] < w) lo = mid + 1; else hi = mid;
-        }
-        if (lo < cl && s_a[lo] == w) {
-            atomicAdd(&s_cnt[lo], 1u);               // c -> w
-            atomicAdd(&t[ws.qk[lane]], 1u);          // x -> w
+        const int p = staged_find(S, ws.qw[lane]);
+        if (p >= 0) {
+            atomicAdd(&S.cnt[p], 1u);                 // c -> w
+            atomicAdd(&t[ws.qk[lane]], 1u);           // x -> w
             atomicAdd(&ws.rowhits[ws.qs[lane]], 1u);  // x -> c or c -> x, credited per row below
         }
     }
     __syncwarp();
 }
 
+// One filter test per lane (w < 0: no id) and the push of the positives to the
+// warp's queue, which is drained 32 at a time.  Called by every lane.  An id
+// equal to c can only occur in a V-mode row N+(x), where it is the edge x -> c.
+__device__ __forceinline__ void probe_step(int32_t w, int64_t k, int slot, int32_t c, const Staged &S,
+                                           uint32_t *t, WarpScratch &ws, int &qn) {
+    const unsigned lane = lane_id();
+    bool pos = false;
+    if (w >= 0) {
+        if (w == c) ws.jpos[slot] = k;
+        const uint32_t h = fhash(w, S.fb);
+        pos = (S.filt[h >> 5] >> (h & 31)) & 1u;
+    }
+    const unsigned pm = __ballot_sync(FULL, pos);
+    if (pos) {
+        const int at = qn + __popc(pm & ((1u << lane) - 1u));
+        ws.qw[at] = w;
+        ws.qk[at] = k;
+        ws.qs[at] = slot;
+    }
+    qn += __popc(pm);
+    if (qn >= 32) {
+        __syncwarp();
+        drain(ws, 32, S, t);
+        if ((int)lane < qn - 32) {
+            ws.qw[lane] = ws.qw[32 + lane];
+            ws.qk[lane] = ws.qk[32 + lane];
+            ws.qs[lane] = ws.qs[32 + lane];
+        }
+        qn -= 32;
+        __syncwarp();
+    }
+}
+
 // One warp processes candidates q0 .. min(q0 + 32, qend) - 1 of centre c
-// against the staged chunk (s_a, cl, filter).  U-mode row hits are credited
-// to c -> x through s_cnt[q] when uv_local (the whole N+(c) is staged) or
-// through t otherwise; V-mode row hits to x -> c at the position of c in N+(x).
+// against the staged chunk S.  Rows longer than SHORT_ROW are read one at a
+// time by the whole warp; the shorter ones are laid end to end over the lanes
+// (each lane finds the row of its id by a 5-step shuffle search over the
+// rows' start offsets).  U-mode row hits are credited to c -> x through
+// S.cnt[q] when uv_local (the whole N+(c) is staged) or through t otherwise;
+// V-mode row hits to x -> c at the position of c in N+(x).
 __device__ __forceinline__ void process_batch(const int64_t *off, const int32_t *col, const uint32_t *flags,
                                               const int64_t *ooff, const int32_t *ocol, uint32_t *t, int32_t c,
                                               int64_t cb, int64_t du, int64_t q0, int64_t qend, bool chunked,
-                                              const int32_t *s_a, int cl, uint32_t *s_cnt, const uint32_t *filt,
-                                              int fb, bool uv_local, WarpScratch &ws, unsigned long long *ctr) {
+                                              const Staged &S, bool uv_local, WarpScratch &ws,
+                                              unsigned long long *ctr) {
     const unsigned lane = lane_id();
-    const unsigned lt = (1u << lane) - 1u;
     const int64_t q = q0 + lane;
     Cand cd{0, -1, 0, false};
-    if (q < qend) cd = load_cand(off, col, flags, ooff, ocol, c, cb, du, q, chunked, s_a[0], s_a[cl - 1]);
+    if (q < qend) cd = load_cand(off, col, flags, ooff, ocol, c, cb, du, q, chunked, S.a[0], S.a[S.cl - 1]);
     ws.rowhits[lane] = 0u;
     ws.jpos[lane] = cd.jpos;
     __syncwarp();
-    unsigned todo = __ballot_sync(FULL, cd.len > 0);
     int qn = 0;
+    // long rows, one after another
+    unsigned todo = __ballot_sync(FULL, cd.len > SHORT_ROW);
     while (todo) {
         const int src = __ffs(todo) - 1;
         todo &= todo - 1;
         const int64_t rs = __shfl_sync(FULL, cd.rs, src);
         const int len = __shfl_sync(FULL, cd.len, src);
-        const bool vm = q0 + src >= du;
-        // UNROLL ids per lane per step: all loads are issued before any is used
         for (int base = 0; base < len; base += 32 * UNROLL) {
             int32_t w[UNROLL];
 #pragma unroll
-            for (int j = 0; j < UNROLL; ++j) {
+            for (int j = 0; j < UNROLL; ++j) {   // all loads issued before any is used
                 const int i = base + 32 * j + (int)lane;
                 w[j] = i < len ? __ldg(&ocol[rs + i]) : -1;
             }
 #pragma unroll
-            for (int j = 0; j < UNROLL; ++j) {
-                const int i = base + 32 * j + (int)lane;
-                bool pos = false;
-                if (w[j] >= 0) {
-                    if (vm && w[j] == c) ws.jpos[src] = rs + i;
-                    const uint32_t h = fhash(w[j], fb);
-                    pos = (filt[h >> 5] >> (h & 31)) & 1u;
-                }
-                const unsigned pm = __ballot_sync(FULL, pos);
-                if (pos) {
-                    const int slot = qn + __popc(pm & lt);
-                    ws.qw[slot] = w[j];
-                    ws.qk[slot] = rs + i;
-                    ws.qs[slot] = src;
-                }
-                qn += __popc(pm);
-                if (qn >= 32) {
-                    __syncwarp();
-                    drain(ws, 32, s_a, cl, s_cnt, t);
-                    if ((int)lane < qn - 32) {
-                        ws.qw[lane] = ws.qw[32 + lane];
-                        ws.qk[lane] = ws.qk[32 + lane];
-                        ws.qs[lane] = ws.qs[32 + lane];
-                    }
-                    qn -= 32;
-                    __syncwarp();
-                }
-            }
+            for (int j = 0; j < UNROLL; ++j)
+                probe_step(w[j], rs + base + 32 * j + (int)lane, src, c, S, t, ws, qn);
         }
     }
+    // short rows, packed end to end
+    const int slen = (cd.len > 0 && cd.len <= SHORT_ROW) ? cd.len : 0;
+    int incl = slen;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if ((int)lane >= o) incl += y;
+    }
+    const int sstart = incl - slen;
+    const int stotal = __shfl_sync(FULL, incl, 31);
+    for (int e0 = 0; e0 < stotal; e0 += 32 * UNROLL) {
+        int32_t w[UNROLL];
+        int64_t kk[UNROLL];
+        int own[UNROLL];
+#pragma unroll
+        for (int j = 0; j < UNROLL; ++j) {
+            const int e = e0 + 32 * j + (int)lane;
+            int p = 0;                           // last lane whose row starts at or before e
+#pragma unroll
+            for (int st = 16; st >= 1; st >>= 1) {
+                const int sp = __shfl_sync(FULL, sstart, p + st);
+                if (sp <= e) p += st;
+            }
+            const int64_t prs = __shfl_sync(FULL, cd.rs, p);
+            const int pst = __shfl_sync(FULL, sstart, p);
+            own[j] = p;
+            kk[j] = prs + (e - pst);
+            w[j] = e < stotal ? __ldg(&ocol[kk[j]]) : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < UNROLL; ++j) probe_step(w[j], kk[j], own[j], c, S, t, ws, qn);
+    }
     __syncwarp();
-    if (qn) drain(ws, qn, s_a, cl, s_cnt, t);
+    if (qn) drain(ws, qn, S, t);
     const uint32_t hits = ws.rowhits[lane];
     if (hits) {
         if (q < du) {
-            if (uv_local) atomicAdd(&s_cnt[q], hits);       // c -> x (whole N+(c) staged)
+            if (uv_local) atomicAdd(&S.cnt[q], hits);       // c -> x (whole N+(c) staged)
             else atomicAdd(&t[cb + q], hits);               // c -> x
         } else {
             const int64_t jp = ws.jpos[lane];
@@ -280,10 +357,11 @@ __device__ __forceinline__ void process_batch(const int64_t *off, const int32_t 
 // ------------------------------------------------------------------ warp visits
 
 constexpr int W_FB = 14;                             // warp filter: 2^14 bits = 2 KB
-constexpr int W_SLICE = (1 << W_FB) / 32 + 2 * W_MAX; // words per warp: filter, s_a, s_cnt
+constexpr int W_DIR = 128;                           // warp directory buckets
+constexpr int W_SLICE = (1 << W_FB) / 32 + 2 * W_MAX + (W_DIR + 2) / 2;   // words per warp
 
 // One warp, one visit of a centre with d+(c) <= W_MAX, on the warp's own
-// slice of shared memory.
+// slice of shared memory: filter, ids, counters, directory.
 __device__ __forceinline__ void warp_visit(const int64_t *off, const int32_t *col, const uint32_t *flags,
                                            const int64_t *ooff, const int32_t *ocol, uint32_t *t, uint64_t task,
                                            int32_t *slice, WarpScratch &ws, unsigned long long *ctr) {
@@ -291,6 +369,7 @@ __device__ __forceinline__ void warp_visit(const int64_t *off, const int32_t *co
     uint32_t *filt = reinterpret_cast<uint32_t *>(slice);
     int32_t *s_a = slice + (1 << W_FB) / 32;
     uint32_t *s_cnt = reinterpret_cast<uint32_t *>(s_a + W_MAX);
+    uint16_t *dir = reinterpret_cast<uint16_t *>(s_a + 2 * W_MAX);
     const int32_t c = (int32_t)(task >> 32);
     const int64_t vis = (int64_t)(task & VIS_MASK);
     const int64_t cb = ooff[c];
@@ -299,18 +378,17 @@ __device__ __forceinline__ void warp_visit(const int64_t *off, const int32_t *co
     const int64_t ncand = du + (deg > du ? deg : 0);
     const int64_t vl = visit_len(du);
     const int64_t qbeg = vis * vl, qend = min(ncand, qbeg + vl);
-    const int fb = filter_bits(du, W_FB);
-    for (int i = (int)lane; i < (1 << fb) / 32; i += 32) filt[i] = 0u;
+    Staged S{s_a, du, s_cnt, filt, filter_bits(du, W_FB), dir, 0, 0, 0};
+    for (int i = (int)lane; i < (1 << S.fb) / 32; i += 32) filt[i] = 0u;
     for (int i = (int)lane; i < du; i += 32) {
         s_a[i] = ocol[cb + i];
         s_cnt[i] = 0u;
     }
     __syncwarp();
-    build_filter(s_a, filt, du, fb, (int)lane, 32);
+    index_staged(S, filt, dir, W_DIR, (int)lane, 32);
     __syncwarp();
     for (int64_t q0 = qbeg; q0 < qend; q0 += 32)
-        process_batch(off, col, flags, ooff, ocol, t, c, cb, du, q0, qend, false, s_a, du, s_cnt, filt, fb, true,
-                      ws, ctr);
+        process_batch(off, col, flags, ooff, ocol, t, c, cb, du, q0, qend, false, S, true, ws, ctr);
     __syncwarp();
     for (int i = (int)lane; i < du; i += 32) {
         const uint32_t cv = s_cnt[i];
@@ -322,7 +400,8 @@ __device__ __forceinline__ void warp_visit(const int64_t *off, const int32_t *co
 // ------------------------------------------------------------------ block visits
 
 constexpr int B_FB = 18;                             // block filter: 2^18 bits = 32 KB
-constexpr int B_WORDS = (1 << B_FB) / 32 + 2 * S_CHUNK;
+constexpr int B_DIR = S_CHUNK;                       // block directory buckets
+constexpr int B_WORDS = (1 << B_FB) / 32 + 2 * S_CHUNK + (B_DIR + 2) / 2;
 static_assert(B_WARPS * W_SLICE <= B_WORDS, "warp slices must fit the block buffer");
 
 // Persistent kernel: every block first drains the block-visit list (pulled
@@ -335,6 +414,7 @@ k_support(const int64_t *off, const int32_t *col, const uint32_t *flags, const i
     uint32_t *filt = reinterpret_cast<uint32_t *>(smem);              // 2^B_FB bits
     int32_t *s_a = smem + (1 << B_FB) / 32;                           // S_CHUNK ids
     uint32_t *s_cnt = reinterpret_cast<uint32_t *>(s_a + S_CHUNK);      // S_CHUNK counters
+    uint16_t *dir = reinterpret_cast<uint16_t *>(s_a + 2 * S_CHUNK);    // B_DIR + 1 bucket starts
     __shared__ WarpScratch s_ws[B_WARPS];
     __shared__ long long s_item;
     __shared__ int s_next;
@@ -361,23 +441,23 @@ k_support(const int64_t *off, const int32_t *col, const uint32_t *flags, const i
         const bool chunked = du > S_CHUNK;
         for (int64_t c0 = 0; c0 < du; c0 += S_CHUNK) {
             const int cl = (int)min((int64_t)S_CHUNK, du - c0);
-            const int fb = filter_bits(cl, B_FB);
-            for (int i = threadIdx.x; i < (1 << fb) / 32; i += B_THREADS) filt[i] = 0u;
+            Staged S{s_a, cl, s_cnt, filt, filter_bits(cl, B_FB), dir, 0, 0, 0};
+            for (int i = threadIdx.x; i < (1 << S.fb) / 32; i += B_THREADS) filt[i] = 0u;
             for (int i = threadIdx.x; i < cl; i += B_THREADS) {
                 s_a[i] = ocol[cb + c0 + i];
                 s_cnt[i] = 0u;
             }
             if (threadIdx.x == 0) s_next = 0;
             __syncthreads();
-            build_filter(s_a, filt, cl, fb, threadIdx.x, B_THREADS);
+            index_staged(S, filt, dir, B_DIR, threadIdx.x, B_THREADS);
             __syncthreads();
             for (;;) {
                 int b = 0;
                 if (lane == 0) b = atomicAdd(&s_next, 32);
                 b = __shfl_sync(FULL, b, 0);
                 if (qbeg + b >= qend) break;
-                process_batch(off, col, flags, ooff, ocol, t, c, cb, du, qbeg + b, qend, chunked, s_a, cl, s_cnt,
-                              filt, fb, false, ws, ctr);
+                process_batch(off, col, flags, ooff, ocol, t, c, cb, du, qbeg + b, qend, chunked, S, false, ws,
+                              ctr);
             }
             __syncthreads();
             for (int i = threadIdx.x; i < cl; i += B_THREADS) {

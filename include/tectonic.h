@@ -180,6 +180,37 @@ tec_status tec_set_stage_events(tec_graph *g, void *const *events, int count);
  * either may be NULL.  Row u lists N+(u) ascending. */
 tec_status tec_oriented_csr(tec_graph *g, int64_t *ooff_out, int32_t *ocol_out);
 
+/* ---------------------------------------------------------------- no allocation */
+
+/* Largest vertex count tec_components_noalloc accepts. */
+#define TEC_NOALLOC_MAX_VERTICES 4194304
+
+/* Connected components of an edge list, for callers that cannot allocate
+ * device memory when they need the result: a host application that owns the
+ * GPU memory budget, a latency-critical path that cannot pay for a
+ * cudaMalloc / cudaFree (either may synchronise the device), or code that must
+ * not fail for lack of memory halfway through.  The paper has no counterpart;
+ * it is the union-find of tec_components with its scratch in a fixed
+ * file-scope device array instead of graph-owned memory.
+ *
+ * n <= TEC_NOALLOC_MAX_VERTICES vertices (TEC_EINVAL beyond), m edges
+ * (eu[e], ev[e]) given as device int32 arrays; keep (device, m bytes) selects
+ * the edges to use, NULL uses all.  labels_out (device, n int32) receives the
+ * smallest vertex id of each vertex's component; ncomp_out (host, may be NULL)
+ * the number of components.  Runs on `stream` and waits for it; an endpoint
+ * outside [0, n) gives TEC_EINVAL.
+ *
+ * Allocates nothing: the union-find parents live in one device array of
+ * TEC_NOALLOC_MAX_VERTICES int32 (16 MiB) that every GPU loading the library
+ * holds until the process exits.  The first call on a device looks up that
+ * array's device address, so make it before any stream capture.  All calls on
+ * a device share the array and each call re-initialises it; calls whose GPU
+ * work overlaps (other streams, other host threads) race on it and must be
+ * serialised by the caller. */
+tec_status tec_components_noalloc(int64_t n, int64_t m, const int32_t *eu, const int32_t *ev,
+                                  const uint8_t *keep, int32_t *labels_out, int64_t *ncomp_out,
+                                  void *stream);
+
 #ifdef __cplusplus
 }
 #endif

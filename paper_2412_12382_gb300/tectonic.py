@@ -57,7 +57,26 @@ SIGNATURES = {
     "tec_oriented_csr": ([_P, _P, _P], ctypes.c_int),
     "tec_launch_count": ([], ctypes.c_longlong),
     "tec_set_stage_events": ([_P, ctypes.POINTER(_P), ctypes.c_int], ctypes.c_int),
+    "tec_components_noalloc": ([_I64, _I64, _P, _P, _P, _P, _PI64, _P], ctypes.c_int),
 }
+
+NOALLOC_MAX_VERTICES = 4194304
+
+
+def components_noalloc(n: int, eu, ev, keep=None, labels=None, stream=None):
+    """Components of the edge list (eu, ev) (CUDA int32 tensors; keep: optional
+    uint8 mask) through the entry point that allocates no device memory.
+    Returns (labels, number of components)."""
+    torch = _require_cuda()
+    lib = load_library()
+    if labels is None:
+        labels = torch.empty(max(n, 0), dtype=torch.int32, device="cuda")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    nc = ctypes.c_int64(-1)
+    check(lib.tec_components_noalloc(int(n), int(eu.numel()), _ptr(eu), _ptr(ev), _ptr(keep), _ptr(labels),
+                                     ctypes.byref(nc), _P(stream.cuda_stream)))
+    return labels, nc.value
 
 
 def library_path() -> str:

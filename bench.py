@@ -34,6 +34,8 @@ WORKLOADS = {
                    name="R-MAT scale 26, edge factor 32, (0.57,0.19,0.19,0.05), seed 3; Tectonic full pass at 1/10"),
     "rmat20": dict(kind="rmat", scale=20, edge_factor=16, seed=2, p=1, q=10,
                    name="R-MAT scale 20, edge factor 16, (0.57,0.19,0.19,0.05), seed 2; Tectonic full pass at 1/10"),
+    "rmat22": dict(kind="rmat", scale=22, edge_factor=16, seed=2, p=1, q=10,
+                   name="R-MAT scale 22, edge factor 16, (0.57,0.19,0.19,0.05), seed 2; Tectonic full pass at 1/10"),
     "sbm": dict(kind="sbm", p=3, q=50,
                 name="planted-partition SBM n=2000, 4x500, p_in=0.05, p_out=0.002, seed 1; Tectonic at 3/50"),
 }
@@ -41,7 +43,8 @@ WORKLOADS = {
 # DRAM bytes per launch of the triangle-count stage from an ncu capture, per
 # unit of algorithmic bytes, valid only for the support.cu it was taken on
 # (see profiles/).  None until a capture exists for the current source.
-TRAFFIC_CAPTURE = {"support_sha": None, "dram_per_alg_byte": None}
+TRAFFIC_CAPTURE = {"support_sha": "539a64f0de07566b", "dram_per_alg_byte": 82.2969 / 49.162954,
+                   "source": "ncu DRAM bytes of k_support at R-MAT scale 22, scaled by algorithmic bytes"}
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -383,7 +386,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "triangle-count stage (support kernels)",
-                         "alg_bytes_per_launch": B_sup, "peak_kind": peak_kind},
+                         "alg_bytes_per_launch": B_sup, "peak_kind": peak_kind,
+                         "traffic_source": TRAFFIC_CAPTURE["source"] if traffic else None},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "gpu_launches_per_step": launches / args.steps, "clocks": clocks,
         }

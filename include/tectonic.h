@@ -150,6 +150,20 @@ tec_status tec_prune(tec_graph *g, tec_measure measure, int64_t p, int64_t q, ui
  * prune has run. */
 tec_status tec_components(tec_graph *g, int32_t *labels_out, int64_t *ncomp_out);
 
+/* Components at k thresholds at once: for each threshold i, the labels (and
+ * number of components) that tec_prune(p[i], q[i]) + tec_components would give,
+ * through a maximum spanning forest of the edge levels (the number of
+ * thresholds each edge survives) and one offline union-find sweep over the
+ * forest edges, highest level first.  Thresholds may come in any order and
+ * may repeat; 1 <= k <= 127; p, q are HOST arrays.  labels_out (device,
+ * k x n int32, row i for threshold i).  A batch of graphs is loaded as one
+ * disjoint union: seg_off (device, nseg+1 int64 vertex offsets of the graphs,
+ * or NULL) makes every label relative to its graph's first vertex, and
+ * ncomp_out (HOST, may be NULL; waits) receives k x nseg component counts (k
+ * counts without segments).  Replaces the last prune's mask state. */
+tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q, int k,
+                     const int64_t *seg_off, int nseg, int32_t *labels_out, int64_t *ncomp_out);
+
 /* Algorithm 1 end to end on the loaded graph: orientation, triangle counts,
  * similarity, pruning at p/q and components, with pruning and the union-find
  * hooking fused into one kernel.  Same outputs as tec_prune + tec_components

@@ -5,7 +5,9 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <algorithm>
 #include <new>
+#include <numeric>
 #include <vector>
 
 #include "tec_internal.cuh"
@@ -61,7 +63,8 @@ tec_status dalloc(T **p, int64_t count, const char *what) {
 
 void free_graph_memory(tec_graph *g) {
     void *ptrs[] = {g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->parent, g->tasks,
-                    g->flags, g->tile_cnt, g->tile_base, g->bsum, g->uoff, g->ucnt, g->labels, g->ctr};
+                    g->flags, g->tile_cnt, g->tile_base, g->bsum, g->uoff, g->ucnt, g->labels, g->lvl, g->best,
+                    g->fu, g->fv, g->bucket, g->thr, g->sw_ncomp, g->ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (g->ctr_host) cudaFreeHost(g->ctr_host);
@@ -461,6 +464,81 @@ tec_status tec_full_pass_host(tec_graph *g, const int64_t *row_off_host, const i
                                  g->stream));
     TEC_TRY(read_counters(g));
     if (ncomp_out) *ncomp_out = (int64_t)g->ctr_host[C_NCOMP];
+    return TEC_OK;
+}
+
+tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q, int k,
+                     const int64_t *seg_off, int nseg, int32_t *labels_out, int64_t *ncomp_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (k < 1 || k > 127) return set_error(TEC_EINVAL, "k must be in [1, 127] (got %d)", k);
+    if (!p || !q) return set_error(TEC_EINVAL, "threshold arrays are NULL");
+    if (!labels_out && g->n > 0) return set_error(TEC_EINVAL, "labels_out is NULL");
+    if (seg_off && nseg < 1) return set_error(TEC_EINVAL, "nseg must be >= 1 with a segment table");
+    bool wide = false;
+    for (int i = 0; i < k; ++i) {
+        TEC_TRY(check_threshold((int)measure, p[i], q[i]));
+        wide = wide || needs_wide(p[i], q[i]);
+    }
+    DeviceGuard dg(g->device);
+    const int nsl = seg_off ? nseg : 1;
+    // thresholds in ascending value, equal values kept in input order
+    std::vector<int> order(k);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return (__int128)p[a] * q[b] < (__int128)p[b] * q[a]; });
+    std::vector<int64_t> hthr(2 * k);
+    for (int i = 0; i < k; ++i) {
+        hthr[i] = p[order[i]];
+        hthr[k + i] = q[order[i]];
+    }
+    if (!g->lvl) TEC_TRY(dalloc(&g->lvl, g->m_cap, "edge levels"));
+    if (!g->best) TEC_TRY(dalloc(&g->best, g->n_cap, "forest offers"));
+    if (!g->fu) TEC_TRY(dalloc(&g->fu, g->n_cap, "forest edges"));
+    if (!g->fv) TEC_TRY(dalloc(&g->fv, g->n_cap, "forest edges"));
+    if (!g->bucket) TEC_TRY(dalloc(&g->bucket, 3 * 127 + 4, "level buckets"));
+    if (!g->thr) TEC_TRY(dalloc(&g->thr, 2 * 127, "thresholds"));
+    if (g->sw_ncomp_cap < (int64_t)k * nsl) {
+        if (g->sw_ncomp) cudaFree(g->sw_ncomp);
+        g->sw_ncomp = nullptr;
+        g->sw_ncomp_cap = 0;
+        TEC_TRY(dalloc(&g->sw_ncomp, (int64_t)k * nsl, "component counts"));
+        g->sw_ncomp_cap = (int64_t)k * nsl;
+    }
+    cudaStream_t s = g->stream;
+    TEC_CUDA(cudaMemcpyAsync(g->thr, hthr.data(), hthr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    TEC_TRY(ensure_support(g));
+    TEC_CUDA(launch_levels(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, (int)measure, g->thr, g->thr + k, k, wide,
+                           g->lvl, g->ctr, s));
+    // Boruvka rounds of the maximum spanning forest
+    g->pruned = g->hooked = false;
+    TEC_CUDA(launch_cc_init(g->parent, g->n, s));
+    if (g->n > 0) TEC_CUDA(cudaMemsetAsync(g->best, 0, (size_t)g->n * sizeof(unsigned long long), s));
+    int round = 0;
+    for (; round < 64; ++round) {
+        TEC_TRY(reset_counter(g, C_CHANGED));
+        TEC_CUDA(launch_msf_round(g->ooff, g->ocol, g->lvl, g->n, g->m, g->parent, g->best, g->ctr, s));
+        TEC_TRY(read_counters(g));
+        if (g->ctr_host[C_CHANGED] == 0) break;
+    }
+    if (round == 64) return set_error(TEC_ETIMEOUT, "the spanning forest did not converge in 64 rounds");
+    // offline sweep over the forest edges, highest level first
+    TEC_CUDA(launch_forest_buckets(g->ooff, g->ocol, g->lvl, g->n, g->m, k, g->bucket, g->fu, g->fv, s));
+    TEC_CUDA(launch_cc_init(g->parent, g->n, s));
+    TEC_CUDA(cudaMemsetAsync(g->sw_ncomp, 0, (size_t)k * nsl * sizeof(unsigned long long), s));
+    for (int L = k; L >= 1; --L) {
+        const int dst = order[L - 1];
+        TEC_CUDA(launch_sweep_level(g->fu, g->fv, g->bucket, k, L, g->n, g->parent,
+                                    labels_out + (int64_t)dst * g->n, seg_off, nseg,
+                                    g->sw_ncomp + (int64_t)dst * nsl, g->ctr, s));
+    }
+    if (ncomp_out) {
+        std::vector<unsigned long long> hn((size_t)k * nsl);
+        TEC_CUDA(cudaMemcpyAsync(hn.data(), g->sw_ncomp, hn.size() * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, s));
+        TEC_TRY(read_counters(g));
+        for (size_t i = 0; i < hn.size(); ++i) ncomp_out[i] = (int64_t)hn[i];
+    }
     return TEC_OK;
 }
 

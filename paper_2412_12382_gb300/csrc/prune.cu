@@ -16,18 +16,6 @@
 namespace tec {
 namespace {
 
-constexpr int64_t NARROW_LIMIT = (int64_t)1 << 28;
-
-template <bool WIDE>
-__device__ __forceinline__ bool keep_edge(int measure, uint32_t tt, int64_t s, int64_t p, int64_t q) {
-    if (measure == TEC_TECTONIC) {
-        if (WIDE) return (__int128)tt * q >= (__int128)p * s;
-        return (int64_t)tt * q >= p * s;
-    }
-    const int64_t tw = 3 * (int64_t)tt + 2 - s;
-    if (WIDE) return (__int128)tw * q >= (__int128)p;
-    return tw * q >= p;
-}
 
 template <bool HOOK, bool WIDE>
 __global__ void __launch_bounds__(TILE_THREADS)
@@ -134,7 +122,7 @@ cudaError_t launch_prune(const int64_t *ooff, const int32_t *ocol, const int32_t
                          unsigned long long *ctr, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)ceil_div(m, TILE);
-    const bool wide = !(a.p > -NARROW_LIMIT && a.p < NARROW_LIMIT && a.q < NARROW_LIMIT);
+    const bool wide = needs_wide(a.p, a.q);
     if (a.hook) {
         if (wide) k_prune<true, true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, a.measure, a.p, a.q, keep, parent, ctr);
         else k_prune<true, false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, a.measure, a.p, a.q, keep, parent, ctr);

@@ -33,6 +33,7 @@ enum Ctr : int {
     C_NBTASK = 4,
     C_NEXT = 5,
     C_NEXTW = 6,
+    C_CHANGED = 7,
     C_COUNT = 16
 };
 
@@ -120,6 +121,20 @@ cudaError_t launch_export(const int64_t *off, const int32_t *col, const int32_t 
 cudaError_t launch_upper_counts(const int64_t *off, const int32_t *col, int64_t n, int32_t *cnt,
                                 cudaStream_t s);
 
+// sweep.cu: levels (number of sorted thresholds each edge survives), Boruvka
+// rounds of the maximum spanning forest (forest edges get bit 7 of lvl), the
+// level buckets of the forest edges, and one union + snapshot step per level.
+cudaError_t launch_levels(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
+                          int64_t n, int64_t m, int measure, const int64_t *tp, const int64_t *tq, int k, bool wide,
+                          uint8_t *lvl, unsigned long long *ctr, cudaStream_t s);
+cudaError_t launch_msf_round(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int64_t m,
+                             int32_t *parent, unsigned long long *best, unsigned long long *ctr, cudaStream_t s);
+cudaError_t launch_forest_buckets(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_t n, int64_t m,
+                                  int k, unsigned long long *bucket, int32_t *fu, int32_t *fv, cudaStream_t s);
+cudaError_t launch_sweep_level(const int32_t *fu, const int32_t *fv, const unsigned long long *bucket, int k, int L,
+                               int64_t n, int32_t *parent, int32_t *labels, const int64_t *seg_off, int nseg,
+                               unsigned long long *ncomp, unsigned long long *ctr, cudaStream_t s);
+
 // cc.cu
 cudaError_t launch_cc_init(int32_t *parent, int64_t n, cudaStream_t s);
 cudaError_t launch_cc_hook(const int64_t *ooff, const int32_t *ocol, const uint32_t *keep,
@@ -150,6 +165,26 @@ __device__ __forceinline__ int64_t row_search(const int64_t *off, int64_t lo, in
 // Orientation order: u before v iff (deg u, u) < (deg v, v).
 __device__ __forceinline__ bool rank_less(int32_t du, int64_t u, int32_t dv, int64_t v) {
     return du < dv || (du == dv && u < v);
+}
+
+// Algorithm 1's survival test sim(e) >= p/q in exact integers, given
+// t = t(u,v) and s = deg u + deg v (q > 0):
+//   Tectonic (Table 1): t*q >= p*s;   TW (Eq. 1): (3t + 2 - s)*q >= p.
+// All products fit int64 when |p|, q < 2^28; WIDE uses 128-bit products.
+template <bool WIDE>
+__device__ __forceinline__ bool keep_edge(int measure, uint32_t tt, int64_t s, int64_t p, int64_t q) {
+    if (measure == TEC_TECTONIC) {
+        if (WIDE) return (__int128)tt * q >= (__int128)p * s;
+        return (int64_t)tt * q >= p * s;
+    }
+    const int64_t tw = 3 * (int64_t)tt + 2 - s;
+    if (WIDE) return (__int128)tw * q >= (__int128)p;
+    return tw * q >= p;
+}
+
+inline bool needs_wide(int64_t p, int64_t q) {
+    const int64_t lim = (int64_t)1 << 28;
+    return !(p > -lim && p < lim && q < lim);
 }
 
 __device__ __forceinline__ void flag_status(unsigned long long *ctr, uint32_t bit) {
@@ -187,6 +222,14 @@ struct tec_graph {
     int64_t *uoff = nullptr;        // export only, allocated on first export
     int32_t *ucnt = nullptr;        // export only
     int32_t *labels = nullptr;      // host-buffer pass only, allocated on first use
+    // sweep scratch, allocated on first sweep
+    uint8_t *lvl = nullptr;         // m: level of each oriented edge, bit 7 = forest edge
+    unsigned long long *best = nullptr;   // n: Boruvka offers
+    int32_t *fu = nullptr, *fv = nullptr; // n: forest edges bucketed by level
+    unsigned long long *bucket = nullptr; // 3k+4 bucket counts / offsets / cursors
+    int64_t *thr = nullptr;         // 2 * 128 sorted thresholds (p then q)
+    unsigned long long *sw_ncomp = nullptr;  // components per level and segment
+    int64_t sw_ncomp_cap = 0;
     unsigned long long *ctr = nullptr;      // device counter block
     unsigned long long *ctr_host = nullptr; // pinned mirror for reads
 

@@ -42,3 +42,24 @@ __device__ __forceinline__ void uf_link(int32_t *parent, int32_t a, int32_t b, u
 }
 
 }  // namespace tec
+
+namespace tec {
+
+// uf_link that also reports whether this call joined two different trees
+// (exactly one caller succeeds for each merge).
+__device__ __forceinline__ bool uf_link_merged(int32_t *parent, int32_t a, int32_t b, unsigned long long *ctr) {
+    int32_t ra = uf_find(parent, a), rb = uf_find(parent, b);
+    for (int it = 0; it < LINK_RETRY_CAP; ++it) {
+        if (ra == rb) return false;
+        const int32_t hi = ra > rb ? ra : rb;
+        const int32_t lo = ra > rb ? rb : ra;
+        const int32_t old = atomicCAS(&parent[hi], hi, lo);
+        if (old == hi) return true;
+        ra = uf_find(parent, old);
+        rb = uf_find(parent, lo);
+    }
+    flag_status(ctr, ST_TIMEOUT);
+    return false;
+}
+
+}  // namespace tec

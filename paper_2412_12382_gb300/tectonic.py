@@ -57,6 +57,7 @@ SIGNATURES = {
     "tec_oriented_csr": ([_P, _P, _P], ctypes.c_int),
     "tec_launch_count": ([], ctypes.c_longlong),
     "tec_set_stage_events": ([_P, ctypes.POINTER(_P), ctypes.c_int], ctypes.c_int),
+    "tec_sweep": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P], ctypes.c_int),
     "tec_components_noalloc": ([_I64, _I64, _P, _P, _P, _P, _PI64, _P], ctypes.c_int),
 }
 
@@ -265,6 +266,22 @@ class Graph:
         nc = ctypes.c_int64(-1)
         check(self._lib.tec_components(self._h, _ptr(labels), ctypes.byref(nc) if count else None))
         return labels, (nc.value if count else None)
+
+    def sweep(self, measure: int, ps, qs, seg_off=None, count: bool = True):
+        """Labels (k x n CUDA int32) and component counts (k, or k x nseg with a
+        segment table of the graphs in a batch) at thresholds ps[i]/qs[i]."""
+        torch = _torch()
+        k = len(ps)
+        hp = np.ascontiguousarray(ps, dtype=np.int64)
+        hq = np.ascontiguousarray(qs, dtype=np.int64)
+        labels = self._empty(k * self.n, torch.int32)
+        nseg = 0 if seg_off is None else seg_off.numel() - 1
+        nc = np.empty(k * max(nseg, 1), dtype=np.int64)
+        check(self._lib.tec_sweep(self._h, int(measure), _ptr(hp), _ptr(hq), k,
+                                  _ptr(seg_off) if seg_off is not None else None, nseg, _ptr(labels),
+                                  _ptr(nc) if count else None))
+        nc = nc.reshape(k, max(nseg, 1)) if nseg else nc
+        return labels.view(k, self.n), (nc if count else None)
 
     def full_pass(self, measure: int, p: int, q: int, labels=None, count: bool = True):
         torch = _torch()

@@ -1,0 +1,88 @@
+"""Multi-threshold sweep (maximum spanning forest + offline union-find) against
+the oracle's definition: one independent prune + components per threshold."""
+import numpy as np
+import pytest
+
+import oracle as O
+from graphgen import planted_partition, rmat_csr, sbm_csr, small
+from graphgen.batch import disjoint_union
+
+pytestmark = pytest.mark.gpu
+
+GRID = [(i, 128) for i in range(1, 65)]          # theta_i = i/128
+
+
+@pytest.fixture(scope="module")
+def tec(cuda_device):
+    import paper_2412_12382_gb300 as pkg
+    from paper_2412_12382_gb300 import build
+    build.build()
+    pkg.load_library()
+    return pkg
+
+
+def _graph(tec, off, col, n_cap=None, nnz_cap=None):
+    import torch
+    return tec.Graph(torch.from_numpy(np.asarray(off, dtype=np.int64)).cuda(),
+                     torch.from_numpy(np.asarray(col, dtype=np.int32)).cuda(), n_cap=n_cap, nnz_cap=nnz_cap)
+
+
+def check_sweep(tec, off, col, measure, thresholds):
+    ps = [p for p, _ in thresholds]
+    qs = [q for _, q in thresholds]
+    ref_lab, ref_nc = O.sweep(off, col, measure, ps, qs)
+    g = _graph(tec, off, col)
+    lab, nc = g.sweep(measure, ps, qs)
+    assert np.array_equal(nc, ref_nc)
+    assert np.array_equal(lab.cpu().numpy(), ref_lab)
+    g.free()
+
+
+def test_sweep_sbm_tectonic_grid(tec):
+    off, col, _ = planted_partition(4, 500, 0.05, 0.002, seed=1)
+    check_sweep(tec, off, col, O.TECTONIC, GRID)
+
+
+def test_sweep_tw_unsorted_with_repeats(tec):
+    off, col, _ = sbm_csr([50, 50], [[0.1, 0.05], [0.05, 0.8]], seed=3)
+    th = [(d, 1) for d in (-10, -30, 0, -2, 4, -30, 12, -40, 2)] + [(3, 50), (-7, 3)]
+    check_sweep(tec, off, col, O.TW, th)
+
+
+def test_sweep_rmat_and_random(tec):
+    off, col = rmat_csr(13, 16, seed=2)
+    check_sweep(tec, off, col, O.TECTONIC, GRID)
+    off, col = small.gnp(400, 0.3, np.random.default_rng(7))
+    check_sweep(tec, off, col, O.TECTONIC, GRID[::3] + [(0, 1), (1, 2)])
+
+
+def test_sweep_degenerate(tec):
+    for off, col in (small.complete(12), small.star(9), small.empty(4), small.two_cliques_bridge(5, 6)):
+        check_sweep(tec, off, col, O.TECTONIC, [(0, 1), (1, 1000), (5, 12), (1, 2), (1, 1)])
+
+
+def test_sweep_batch_of_uneven_graphs(tec):
+    import torch
+    graphs = [planted_partition(3, 40, 0.3, 0.02, seed=s)[:2] for s in (1, 2)]
+    graphs += [rmat_csr(10, 8, seed=5), small.empty(3), small.complete(7), small.gnp(150, 0.1, np.random.default_rng(3))]
+    off, col, seg = disjoint_union(graphs)
+    g = _graph(tec, off, col)
+    lab, nc = g.sweep(O.TECTONIC, [p for p, _ in GRID], [q for _, q in GRID],
+                      seg_off=torch.from_numpy(seg).cuda())
+    lab = lab.cpu().numpy()
+    for gi, (go, gc) in enumerate(graphs):
+        ref_lab, ref_nc = O.sweep(go, gc, O.TECTONIC, [p for p, _ in GRID], [q for _, q in GRID])
+        assert np.array_equal(nc[:, gi], ref_nc)
+        assert np.array_equal(lab[:, seg[gi]:seg[gi + 1]], ref_lab)
+    g.free()
+
+
+def test_sweep_then_prune_components_still_agree(tec):
+    off, col, _ = planted_partition(4, 500, 0.05, 0.002, seed=1)
+    g = _graph(tec, off, col)
+    lab, nc = g.sweep(O.TECTONIC, [1, 3, 9], [40, 50, 128])
+    for i, (p, q) in enumerate(((1, 40), (3, 50), (9, 128))):
+        g.prune(O.TECTONIC, p, q)
+        cl, cn = g.components()
+        assert cn == nc[i] and np.array_equal(cl.cpu().numpy(), lab[i].cpu().numpy())
+    g.free()

@@ -164,6 +164,26 @@ tec_status tec_components(tec_graph *g, int32_t *labels_out, int64_t *ncomp_out)
 tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q, int k,
                      const int64_t *seg_off, int nseg, int32_t *labels_out, int64_t *ncomp_out);
 
+/* Picker features of every graph of a batch (the whole graph if seg_off is
+ * NULL): the 64-bin histogram of Tectonic weights on the grid i/128
+ * (bin = min(63, floor(128 t / (deg u + deg v)))), divided by the graph's edge
+ * count m, then ln(2m/n) and ln(m).  feat_out: device, nseg x 66 float32
+ * (rows of zeros for graphs without edges).  Runs tec_support if needed.  The
+ * paper picks thresholds by rules of thumb (Sec. IV-E); these features feed
+ * the learned picker that replaces them. */
+tec_status tec_features(tec_graph *g, const int64_t *seg_off, int nseg, float *feat_out);
+
+/* Adjusted Rand index (Hubert & Arabie 1985) between k labelings (device,
+ * k x n int32, e.g. the output of tec_sweep, labels relative to each graph
+ * when seg_off is given) and reference blocks truth (device, n int32, block
+ * ids 0..63 within each graph; TEC_EBADGRAPH at the next wait otherwise).
+ * ari_out: device, k x nseg float64 (k values without segments).  Pair counts
+ * are exact integers; the final ratio has a relative error below 1e-15.  The
+ * paper evaluates with matched precision / recall (Sec. IV-A); ARI is the
+ * project's judge of the picker. */
+tec_status tec_ari(tec_graph *g, int k, const int32_t *labels, const int32_t *truth, const int64_t *seg_off, int nseg,
+                   double *ari_out);
+
 /* Algorithm 1 end to end on the loaded graph: orientation, triangle counts,
  * similarity, pruning at p/q and components, with pruning and the union-find
  * hooking fused into one kernel.  Same outputs as tec_prune + tec_components

@@ -64,7 +64,8 @@ tec_status dalloc(T **p, int64_t count, const char *what) {
 void free_graph_memory(tec_graph *g) {
     void *ptrs[] = {g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->parent, g->tasks,
                     g->flags, g->tile_cnt, g->tile_base, g->bsum, g->uoff, g->ucnt, g->labels, g->lvl, g->best,
-                    g->fu, g->fv, g->bucket, g->thr, g->sw_ncomp, g->ctr};
+                    g->fu, g->fv, g->bucket, g->thr, g->sw_ncomp, g->seg_hist, g->ari_sums,
+                    g->ari_size, g->ari_keys, g->ari_cnt, g->ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (g->ctr_host) cudaFreeHost(g->ctr_host);
@@ -162,6 +163,63 @@ tec_status run_full_pass(tec_graph *g, int measure, int64_t p, int64_t q, int32_
 }  // namespace tec
 
 using namespace tec;
+
+namespace tec {
+namespace {
+tec_status ensure_seg_scratch(tec_graph *g, int ns) {
+    if (g->seg_cap >= ns) return TEC_OK;
+    if (g->seg_hist) cudaFree(g->seg_hist);
+    if (g->ari_sums) cudaFree(g->ari_sums);
+    g->seg_hist = nullptr;
+    g->ari_sums = nullptr;
+    g->seg_cap = 0;
+    TEC_TRY(dalloc(&g->seg_hist, (int64_t)ns * 64, "per-graph histograms"));
+    TEC_TRY(dalloc(&g->ari_sums, (int64_t)ns * 3, "per-graph pair sums"));
+    g->seg_cap = ns;
+    return TEC_OK;
+}
+}  // namespace
+}  // namespace tec
+
+extern "C" {
+
+tec_status tec_features(tec_graph *g, const int64_t *seg_off, int nseg, float *feat_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (!feat_out) return set_error(TEC_EINVAL, "feat_out is NULL");
+    if (seg_off && nseg < 1) return set_error(TEC_EINVAL, "nseg must be >= 1 with a segment table");
+    DeviceGuard dg(g->device);
+    const int ns = seg_off ? nseg : 1;
+    TEC_TRY(ensure_seg_scratch(g, ns));
+    TEC_TRY(ensure_support(g));
+    TEC_CUDA(launch_features(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, seg_off, nseg, g->seg_hist, feat_out, g->ctr,
+                             g->stream));
+    return TEC_OK;
+}
+
+tec_status tec_ari(tec_graph *g, int k, const int32_t *labels, const int32_t *truth, const int64_t *seg_off, int nseg,
+                   double *ari_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (k < 1) return set_error(TEC_EINVAL, "k must be >= 1");
+    if ((!labels || !truth) && g->n > 0) return set_error(TEC_EINVAL, "labels or truth is NULL");
+    if (!ari_out) return set_error(TEC_EINVAL, "ari_out is NULL");
+    if (seg_off && nseg < 1) return set_error(TEC_EINVAL, "nseg must be >= 1 with a segment table");
+    DeviceGuard dg(g->device);
+    const int ns = seg_off ? nseg : 1;
+    TEC_TRY(ensure_seg_scratch(g, ns));
+    if (!g->ari_size) TEC_TRY(dalloc(&g->ari_size, g->n_cap, "component sizes"));
+    if (!g->ari_keys) {
+        const int64_t tsize = (int64_t)1 << ari_table_bits(g->n_cap);
+        TEC_TRY(dalloc(&g->ari_keys, tsize, "cell keys"));
+        TEC_TRY(dalloc(&g->ari_cnt, tsize, "cell counts"));
+    }
+    TEC_CUDA(launch_ari(labels, k, truth, g->n, seg_off, nseg, g->seg_hist, g->ari_size, g->ari_keys, g->ari_cnt,
+                        g->ari_sums, ari_out, g->ctr, g->stream));
+    return TEC_OK;
+}
+
+}  // extern "C"
 
 extern "C" {
 

@@ -135,6 +135,15 @@ cudaError_t launch_sweep_level(const int32_t *fu, const int32_t *fv, const unsig
                                int64_t n, int32_t *parent, int32_t *labels, const int64_t *seg_off, int nseg,
                                unsigned long long *ncomp, unsigned long long *ctr, cudaStream_t s);
 
+// eval.cu: picker features per graph and adjusted Rand index per (level, graph).
+cudaError_t launch_features(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
+                            int64_t n, int64_t m, const int64_t *seg_off, int nseg, unsigned int *hist, float *feat,
+                            unsigned long long *ctr, cudaStream_t s);
+int ari_table_bits(int64_t n);
+cudaError_t launch_ari(const int32_t *labels, int k, const int32_t *truth, int64_t n, const int64_t *seg_off, int nseg,
+                       unsigned int *bsz, unsigned int *size, unsigned long long *keys, unsigned int *cnt,
+                       unsigned long long *sums, double *out, unsigned long long *ctr, cudaStream_t s);
+
 // cc.cu
 cudaError_t launch_cc_init(int32_t *parent, int64_t n, cudaStream_t s);
 cudaError_t launch_cc_hook(const int64_t *ooff, const int32_t *ocol, const uint32_t *keep,
@@ -230,6 +239,13 @@ struct tec_graph {
     int64_t *thr = nullptr;         // 2 * 128 sorted thresholds (p then q)
     unsigned long long *sw_ncomp = nullptr;  // components per level and segment
     int64_t sw_ncomp_cap = 0;
+    // features / ARI scratch, grown on demand
+    unsigned int *seg_hist = nullptr;      // nseg x 64 (histogram, block sizes)
+    int64_t seg_cap = 0;
+    unsigned long long *ari_sums = nullptr; // 3 x nseg
+    unsigned int *ari_size = nullptr;      // n_cap
+    unsigned long long *ari_keys = nullptr; // 2^bits cell keys
+    unsigned int *ari_cnt = nullptr;       // 2^bits cell counts
     unsigned long long *ctr = nullptr;      // device counter block
     unsigned long long *ctr_host = nullptr; // pinned mirror for reads
 

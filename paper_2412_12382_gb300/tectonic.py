@@ -58,6 +58,8 @@ SIGNATURES = {
     "tec_launch_count": ([], ctypes.c_longlong),
     "tec_set_stage_events": ([_P, ctypes.POINTER(_P), ctypes.c_int], ctypes.c_int),
     "tec_sweep": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P], ctypes.c_int),
+    "tec_features": ([_P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "tec_ari": ([_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "tec_components_noalloc": ([_I64, _I64, _P, _P, _P, _P, _PI64, _P], ctypes.c_int),
 }
 
@@ -282,6 +284,24 @@ class Graph:
                                   _ptr(nc) if count else None))
         nc = nc.reshape(k, max(nseg, 1)) if nseg else nc
         return labels.view(k, self.n), (nc if count else None)
+
+    def features(self, seg_off=None):
+        """Picker features: (nseg, 66) float32 CUDA tensor (one row without segments)."""
+        torch = _torch()
+        nseg = 0 if seg_off is None else seg_off.numel() - 1
+        f = torch.empty((max(nseg, 1), 66), dtype=torch.float32, device="cuda")
+        check(self._lib.tec_features(self._h, _ptr(seg_off) if seg_off is not None else None, nseg, _ptr(f)))
+        return f
+
+    def ari(self, labels, truth, seg_off=None):
+        """ARI of each row of `labels` (k x n) against `truth` (n): (k, nseg) float64 tensor."""
+        torch = _torch()
+        k = labels.shape[0] if labels.dim() == 2 else 1
+        nseg = 0 if seg_off is None else seg_off.numel() - 1
+        out = torch.empty((k, max(nseg, 1)), dtype=torch.float64, device="cuda")
+        check(self._lib.tec_ari(self._h, k, _ptr(labels.contiguous()), _ptr(truth.contiguous()),
+                                _ptr(seg_off) if seg_off is not None else None, nseg, _ptr(out)))
+        return out
 
     def full_pass(self, measure: int, p: int, q: int, labels=None, count: bool = True):
         torch = _torch()

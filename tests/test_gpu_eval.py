@@ -1,0 +1,95 @@
+"""Picker features and ARI on the GPU against the oracle.
+
+Features are float32 on the device: compared with the oracle's float64 values
+to 1e-6 relative (two float32 roundings and one logf).  ARI: exact integer pair
+counts and a ratio of exact 128-bit integers converted to double; tolerance
+2e-15 absolute (at most a few roundings of a value in [-1, 1])."""
+import numpy as np
+import pytest
+
+import oracle as O
+from graphgen import planted_partition, rmat_csr, sbm_csr, small
+from graphgen.batch import disjoint_union
+
+pytestmark = pytest.mark.gpu
+
+GRID = [(i, 128) for i in range(1, 65)]
+
+
+@pytest.fixture(scope="module")
+def tec(cuda_device):
+    import paper_2412_12382_gb300 as pkg
+    from paper_2412_12382_gb300 import build
+    build.build()
+    pkg.load_library()
+    return pkg
+
+
+def _graph(tec, off, col):
+    import torch
+    return tec.Graph(torch.from_numpy(np.asarray(off, dtype=np.int64)).cuda(),
+                     torch.from_numpy(np.asarray(col, dtype=np.int32)).cuda())
+
+
+def _oracle_features(off, col):
+    eu, ev = O.edge_list(off, col)
+    t, _ = O.edge_counts(off, col, eu, ev)
+    return O.features(off, eu, ev, t)
+
+
+def test_features_single_and_batch(tec):
+    import torch
+    graphs = [planted_partition(4, 500, 0.05, 0.002, seed=1)[:2], rmat_csr(12, 16, seed=4), small.complete(9),
+              small.empty(5), small.two_cliques_bridge(6, 9)]
+    for off, col in graphs[:3]:
+        g = _graph(tec, off, col)
+        f = g.features().cpu().numpy()[0]
+        np.testing.assert_allclose(f, _oracle_features(off, col), rtol=1e-6, atol=0)
+        g.free()
+    off, col, seg = disjoint_union(graphs)
+    g = _graph(tec, off, col)
+    f = g.features(torch.from_numpy(seg).cuda()).cpu().numpy()
+    for i, (go, gc) in enumerate(graphs):
+        np.testing.assert_allclose(f[i], _oracle_features(go, gc), rtol=1e-6, atol=0)
+    g.free()
+
+
+def test_ari_of_sweep_against_planted_blocks(tec):
+    import torch
+    sizes = [[60, 80, 50], [120, 40], [30] * 6]
+    graphs, truths = [], []
+    for s, sz in enumerate(sizes):
+        P = np.full((len(sz), len(sz)), 0.02)
+        np.fill_diagonal(P, 0.3)
+        off, col, blk = sbm_csr(sz, P, seed=40 + s)
+        graphs.append((off, col))
+        truths.append(blk)
+    off, col, seg = disjoint_union(graphs)
+    truth = np.concatenate(truths).astype(np.int32)
+    g = _graph(tec, off, col)
+    segd = torch.from_numpy(seg).cuda()
+    lab, _ = g.sweep(O.TECTONIC, [p for p, _ in GRID], [q for _, q in GRID], seg_off=segd)
+    ari = g.ari(lab, torch.from_numpy(truth).cuda(), segd).cpu().numpy()
+    labh = lab.cpu().numpy()
+    for gi in range(len(graphs)):
+        for L in range(64):
+            ref = O.ari(labh[L, seg[gi]:seg[gi + 1]], truths[gi])
+            assert abs(ari[L, gi] - ref) <= 2e-15, (gi, L, ari[L, gi], ref)
+    g.free()
+
+
+def test_ari_random_labelings(tec):
+    import torch
+    rng = np.random.default_rng(5)
+    off, col = small.gnp(300, 0.05, rng)
+    g = _graph(tec, off, col)
+    n = 300
+    labs = np.stack([rng.integers(0, k, n) for k in (1, 2, 7, 40, 300)] + [np.arange(n)]).astype(np.int32)
+    truth = rng.integers(0, 5, n).astype(np.int32)
+    ari = g.ari(torch.from_numpy(labs).cuda(), torch.from_numpy(truth).cuda()).cpu().numpy()[:, 0]
+    for L in range(len(labs)):
+        assert abs(ari[L] - O.ari(labs[L], truth)) <= 2e-15
+    # identical partitions and the trivial cases score 1
+    same = g.ari(torch.from_numpy(truth[None, :].copy()).cuda(), torch.from_numpy(truth).cuda()).cpu().numpy()
+    assert same[0, 0] == 1.0
+    g.free()

@@ -115,9 +115,68 @@ RmatParams make_params(int scale, uint32_t A, uint32_t AB, uint32_t ABC, uint64_
     return p;
 }
 
+// ---------------------------------------------------------------- DC-SBM
+
+__device__ __forceinline__ uint64_t draw_word(uint64_t key, uint64_t counter) { return mix64(key ^ mix64(counter)); }
+
+// Largest i in [0, len) with a[i] <= x (a non-decreasing, a[0] <= x).
+__device__ __forceinline__ int64_t pick(const long long *a, int64_t len, long long x) {
+    int64_t lo = 0, hi = len - 1;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (a[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_dcsbm(uint64_t key, int64_t samples, int n, int k, uint64_t mu_cut, const int *block,
+                        const int *order, const long long *cum, const long long *bstart, long long voff,
+                        long long *keys) {
+    const unsigned long long W = (unsigned long long)cum[n];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < samples;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t w0 = draw_word(key, 4ull * e), w1 = draw_word(key, 4ull * e + 1);
+        const uint64_t w2 = draw_word(key, 4ull * e + 2), w3 = draw_word(key, 4ull * e + 3);
+        int u, v;
+        if ((w0 >> 11) < mu_cut) {
+            const int64_t iu = pick(cum, n + 1, (long long)__umul64hi(w1, W));
+            const int bu = block[order[iu]];
+            const unsigned long long vb = (unsigned long long)(bstart[bu + 1] - bstart[bu]);
+            int64_t iv = iu;
+            if (W - vb != 0) {
+                long long pv = (long long)__umul64hi(w2, W - vb);
+                if (pv >= bstart[bu]) pv += (long long)vb;
+                if (pv > (long long)W - 1) pv = (long long)W - 1;
+                iv = pick(cum, n + 1, pv);
+            }
+            u = order[iu];
+            v = order[iv];
+        } else {
+            const int64_t b = pick(bstart, k + 1, (long long)__umul64hi(w1, W));
+            const unsigned long long vb = (unsigned long long)(bstart[b + 1] - bstart[b]);
+            u = order[pick(cum, n + 1, bstart[b] + (long long)__umul64hi(w2, vb))];
+            v = order[pick(cum, n + 1, bstart[b] + (long long)__umul64hi(w3, vb))];
+        }
+        const long long gu = voff + u, gv = voff + v;
+        keys[2 * e] = u == v ? -1ll : ((gu << 32) | gv);
+        keys[2 * e + 1] = u == v ? -1ll : ((gv << 32) | gu);
+    }
+}
+
 }  // namespace
 
 extern "C" {
+
+// Directed keys (src << 32 | dst, both directions, -1 for self-loops) of the
+// samples of one DC-SBM graph whose vertex arrays are on the device; vertex
+// ids are offset by voff.  keys needs 2 * samples entries.
+int gg_dcsbm(uint64_t key, int64_t samples, int n, int k, uint64_t mu_cut, const int *block, const int *order,
+             const long long *cum, const long long *bstart, long long voff, long long *keys, void *stream) {
+    if (n < 1 || k < 1) return 1;
+    k_dcsbm<<<2048, 256, 0, (cudaStream_t)stream>>>(key, samples, n, k, mu_cut, block, order, cum, bstart, voff, keys);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
 
 // counts[2^bucket_bits] (device, zeroed by the caller) += directed entries per src bucket.
 int gg_rmat_count(int scale, uint64_t nsamples, uint32_t A, uint32_t AB, uint32_t ABC, uint64_t key,

@@ -10,6 +10,8 @@ import os
 import shutil
 import subprocess
 
+import numpy as np
+
 from .prng import STREAM_RMAT, stream_key
 from .rmat import cut_points, feistel_keys
 
@@ -48,6 +50,9 @@ def _load():
         P = ctypes.c_void_p
         lib.gg_rmat_count.argtypes = [i32, u64, u32, u32, u32, u64, P, i32, P, P]
         lib.gg_rmat_emit.argtypes = [i32, u64, u32, u32, u32, u64, P, i32, i32, i32, P, P, ctypes.c_longlong, P]
+        i64 = ctypes.c_int64
+        lib.gg_dcsbm.argtypes = [u64, i64, i32, i32, u64, P, P, P, P, ctypes.c_longlong, P, P]
+        lib.gg_dcsbm.restype = i32
         lib.gg_rmat_count.restype = i32
         lib.gg_rmat_emit.restype = i32
         _lib = lib
@@ -106,3 +111,44 @@ def rmat_csr_gpu(scale: int, edge_factor: int, abc=(0.57, 0.19, 0.19), seed: int
     off = torch.zeros(n + 1, dtype=torch.int64, device=dev)
     torch.cumsum(deg, 0, out=off[1:])
     return off, col
+
+
+def dcsbm_batch_gpu(seeds, n_lo: int = 1000, n_hi: int = 100000):
+    """A batch of DC-SBM graphs (graphgen.dcsbm definition) as one disjoint
+    union, built on the GPU.  Returns CUDA tensors (off int64, col int32,
+    seg_off int64, truth int32 block ids) and the host specs."""
+    import torch
+    from .dcsbm import dcsbm_spec
+    from .prng import STREAM_DCSBM, stream_key
+    lib = _load()
+    dev = torch.device("cuda")
+    specs = [dcsbm_spec(s, n_lo, n_hi) for s in seeds]
+    seg = [0]
+    for sp in specs:
+        seg.append(seg[-1] + sp.n)
+    N = seg[-1]
+    total = sum(sp.samples for sp in specs)
+    keys = torch.empty(2 * total, dtype=torch.int64, device=dev)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    at = 0
+    keep = []
+    for sp, voff in zip(specs, seg[:-1]):
+        arrs = [torch.from_numpy(a).to(dev) for a in (sp.block, sp.order, sp.cum, sp.bstart)]
+        keep.append(arrs)
+        rc = lib.gg_dcsbm(stream_key(sp.seed, STREAM_DCSBM + 3), sp.samples, sp.n, sp.k, sp.mu_cut,
+                          ctypes.c_void_p(arrs[0].data_ptr()), ctypes.c_void_p(arrs[1].data_ptr()),
+                          ctypes.c_void_p(arrs[2].data_ptr()), ctypes.c_void_p(arrs[3].data_ptr()), voff,
+                          ctypes.c_void_p(keys[2 * at].data_ptr()), stream)
+        if rc:
+            raise RuntimeError(f"gg_dcsbm failed ({rc})")
+        at += sp.samples
+    keys = torch.unique(keys[keys >= 0])
+    src = keys >> 32
+    col = (keys & ((1 << 32) - 1)).to(torch.int32)
+    off = torch.zeros(N + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(torch.bincount(src, minlength=N), 0, out=off[1:])
+    truth = torch.from_numpy(np.concatenate([sp.block for sp in specs]).astype(np.int32)).to(dev)
+    seg_off = torch.tensor(seg, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+    del keep
+    return off, col, seg_off, truth, specs

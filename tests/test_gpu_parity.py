@@ -231,3 +231,17 @@ def test_repeated_runs_are_identical(tec):
         assert hnc == ref.ncomp and np.array_equal(hl, ref.labels)
     g.free()
     g2.free()
+
+
+def test_dcsbm_gpu_batch_matches_host(cuda_device):
+    from graphgen.batch import disjoint_union
+    from graphgen.dcsbm import dcsbm_csr
+    from graphgen.gpu import dcsbm_batch_gpu
+    seeds = [1000, 1001, 1002, 20000]
+    host = [dcsbm_csr(s, 1000, 6000) for s in seeds]
+    off, col, seg = disjoint_union([(h[0], h[1]) for h in host])
+    goff, gcol, gseg, gtruth, _ = dcsbm_batch_gpu(seeds, 1000, 6000)
+    assert np.array_equal(gseg.cpu().numpy(), seg)
+    assert np.array_equal(goff.cpu().numpy(), off)
+    assert np.array_equal(gcol.cpu().numpy(), col)
+    assert np.array_equal(gtruth.cpu().numpy(), np.concatenate([h[2] for h in host]))

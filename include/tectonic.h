@@ -184,6 +184,21 @@ tec_status tec_features(tec_graph *g, const int64_t *seg_off, int nseg, float *f
 tec_status tec_ari(tec_graph *g, int k, const int32_t *labels, const int32_t *truth, const int64_t *seg_off, int nseg,
                    double *ari_out);
 
+/* Algorithm 1 for every graph of a batch, each with its own threshold
+ * p[s]/q[s] (DEVICE int64 arrays, nseg entries; an edge belongs to the graph
+ * of its endpoints): pruning with fused union-find hooking, then labels
+ * relative to each graph's first vertex in labels_out (device, n int32).
+ * ncomp_out (HOST, nseg, may be NULL; waits): components per graph.  A
+ * threshold with q <= 0 removes every edge of its graph.  Runs the triangle
+ * counts if needed. */
+tec_status tec_prune_components_batch(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q,
+                                      const int64_t *seg_off, int nseg, int32_t *labels_out, int64_t *ncomp_out);
+
+/* For each of nseg graphs, the first of k rows of ari (device, k x nseg, as
+ * written by tec_ari) with the highest value: best (device, nseg int32, row
+ * index) and, if not NULL, that value (device, nseg float64), on `stream`. */
+tec_status tec_ari_best(const double *ari, int k, int nseg, int32_t *best, double *best_ari, void *stream);
+
 /* Algorithm 1 end to end on the loaded graph: orientation, triangle counts,
  * similarity, pruning at p/q and components, with pruning and the union-find
  * hooking fused into one kernel.  Same outputs as tec_prune + tec_components
@@ -213,6 +228,64 @@ tec_status tec_set_stage_events(tec_graph *g, void *const *events, int count);
  * if needed) into ooff_out (device, n+1 int64) and ocol_out (device, m int32);
  * either may be NULL.  Row u lists N+(u) ascending. */
 tec_status tec_oriented_csr(tec_graph *g, int64_t *ooff_out, int32_t *ocol_out);
+
+/* ---------------------------------------------------------------- learned threshold picker */
+
+/* The paper picks the threshold delta by rules of thumb (Sec. IV-E: the jump
+ * of the largest component, else maximum modularity).  The picker replaces
+ * them with a small network trained on sweeps: inputs are the tec_features
+ * rows, the output y approximates b/64 for the best grid threshold b/128 (the
+ * one of highest ARI), and the prediction is b = clamp(round(64 y), 1, 64).  Network: 66 -> 128 (ReLU) -> 128 (ReLU) -> 1,
+ * float32 parameters in one vector: W1 [128 x 66] row-major, b1 [128],
+ * W2 [128 x 128], b2 [128], w3 [128], b3.  Loss: mean squared error.
+ * Optimiser: Adam with bias correction. */
+#define TEC_PICKER_INPUTS 66
+#define TEC_PICKER_HIDDEN 128
+#define TEC_PICKER_PARAMS 25217
+
+typedef struct tec_picker tec_picker;
+
+/* Creates a picker on the current device with the given HOST initial
+ * parameters (TEC_PICKER_PARAMS floats; NULL = zeros), Adam moments zero.
+ * stream: cudaStream_t (void*) used by every later call. */
+tec_status tec_picker_create(const float *init_params, void *stream, tec_picker **out);
+tec_status tec_picker_free(tec_picker *p);
+
+/* Checkpointing: copies the parameters (and, if not NULL, the Adam moments
+ * and the step count) to / from HOST memory.  set with NULL moments resets
+ * them to zero.  Both wait. */
+tec_status tec_picker_get_params(tec_picker *p, float *params_out, float *adam_m_out, float *adam_v_out,
+                                 int64_t *step_out);
+tec_status tec_picker_set_params(tec_picker *p, const float *params, const float *adam_m, const float *adam_v,
+                                 int64_t step);
+
+/* out[i] = network output for feats row i (device, N x 66 float32 in, N
+ * float32 out).  bf16 != 0 rounds inputs, weights and hidden activations to
+ * bfloat16 before every product (float32 accumulation). */
+tec_status tec_picker_forward(tec_picker *p, const float *feats, int64_t N, int bf16, float *out);
+
+/* Mean squared error of the N samples (device feats N x 66, target N) into
+ * *loss_out (HOST, may be NULL; waits when given) and its gradient with
+ * respect to every parameter into grad_out (device, TEC_PICKER_PARAMS, may be
+ * NULL).  Deterministic: batch sums run in sample order. */
+tec_status tec_picker_loss_grad(tec_picker *p, const float *feats, const float *target, int64_t N, float *loss_out,
+                                float *grad_out);
+
+/* One Adam update with the given gradient (device; NULL = the gradient of the
+ * last tec_picker_loss_grad). */
+tec_status tec_picker_adam_step(tec_picker *p, const float *grad, float lr, float beta1, float beta2, float eps);
+
+/* Trains for `epochs` passes over N samples (device feats / target) in
+ * mini-batches of `batch`, shuffled each epoch by a keyed permutation of
+ * `seed`, Adam(lr, 0.9, 0.999, 1e-8).  loss_out (HOST, epochs floats, may be
+ * NULL): mean batch loss per epoch.  Waits. */
+tec_status tec_picker_train(tec_picker *p, const float *feats, const float *target, int64_t N, int epochs, int batch,
+                            float lr, uint64_t seed, float *loss_out);
+
+/* Grid thresholds from picker outputs y (device, N float32): b =
+ * clamp(round(64 y), 1, 64) (non-finite y gives 1), p_out[i] = b,
+ * q_out[i] = 128 (device int64 arrays), on `stream`. */
+tec_status tec_picker_thresholds(const float *y, int64_t N, int64_t *p_out, int64_t *q_out, void *stream);
 
 /* ---------------------------------------------------------------- no allocation */
 

@@ -219,6 +219,13 @@ tec_status tec_ari(tec_graph *g, int k, const int32_t *labels, const int32_t *tr
     return TEC_OK;
 }
 
+tec_status tec_ari_best(const double *ari, int k, int nseg, int32_t *best, double *best_ari, void *stream) {
+    clear_error();
+    if (k < 1 || nseg < 0 || (nseg > 0 && (!ari || !best))) return set_error(TEC_EINVAL, "bad argument");
+    TEC_CUDA(launch_best_level(ari, k, nseg, best, best_ari, (cudaStream_t)stream));
+    return TEC_OK;
+}
+
 }  // extern "C"
 
 extern "C" {
@@ -596,6 +603,39 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
                                  cudaMemcpyDeviceToHost, s));
         TEC_TRY(read_counters(g));
         for (size_t i = 0; i < hn.size(); ++i) ncomp_out[i] = (int64_t)hn[i];
+    }
+    return TEC_OK;
+}
+
+tec_status tec_prune_components_batch(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q,
+                                      const int64_t *seg_off, int nseg, int32_t *labels_out, int64_t *ncomp_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (measure != TEC_TECTONIC && measure != TEC_TW) return set_error(TEC_EINVAL, "unknown measure %d", (int)measure);
+    if (!p || !q || !seg_off || nseg < 1) return set_error(TEC_EINVAL, "thresholds and segment table are required");
+    if (!labels_out && g->n > 0) return set_error(TEC_EINVAL, "labels_out is NULL");
+    DeviceGuard dg(g->device);
+    if (g->sw_ncomp_cap < nseg) {
+        if (g->sw_ncomp) cudaFree(g->sw_ncomp);
+        g->sw_ncomp = nullptr;
+        g->sw_ncomp_cap = 0;
+        TEC_TRY(dalloc(&g->sw_ncomp, nseg, "component counts"));
+        g->sw_ncomp_cap = nseg;
+    }
+    TEC_TRY(ensure_support(g));
+    TEC_TRY(reset_counter(g, C_KEPT));
+    TEC_CUDA(launch_cc_init(g->parent, g->n, g->stream));
+    TEC_CUDA(launch_prune_seg(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, (int)measure, p, q, seg_off, nseg, true,
+                              g->keep, g->parent, g->ctr, g->stream));
+    g->pruned = g->hooked = true;
+    TEC_CUDA(cudaMemsetAsync(g->sw_ncomp, 0, (size_t)nseg * sizeof(unsigned long long), g->stream));
+    TEC_CUDA(launch_snapshot(g->parent, g->n, labels_out, seg_off, nseg, g->sw_ncomp, g->stream));
+    if (ncomp_out) {
+        std::vector<unsigned long long> hn((size_t)nseg);
+        TEC_CUDA(cudaMemcpyAsync(hn.data(), g->sw_ncomp, hn.size() * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, g->stream));
+        TEC_TRY(read_counters(g));
+        for (int i = 0; i < nseg; ++i) ncomp_out[i] = (int64_t)hn[i];
     }
     return TEC_OK;
 }

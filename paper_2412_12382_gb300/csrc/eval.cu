@@ -163,6 +163,20 @@ __global__ void k_ari_final(const unsigned long long *sums, const unsigned int *
     out[s] = (nv < 2 || den == 0) ? 1.0 : i128_to_double(num) / i128_to_double(den);
 }
 
+// Per graph: the first level of highest ARI (ari is k x nseg).
+__global__ void k_best_level(const double *ari, int k, int nseg, int32_t *best, double *best_ari) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    int bi = 0;
+    double bv = ari[s];
+    for (int L = 1; L < k; ++L) {
+        const double v = ari[(int64_t)L * nseg + s];
+        if (v > bv) { bv = v; bi = L; }
+    }
+    best[s] = bi;
+    if (best_ari) best_ari[s] = bv;
+}
+
 inline unsigned grid_for(int64_t work) {
     const int64_t g = ceil_div(work > 0 ? work : 1, 256);
     return (unsigned)(g < 65536 ? g : 65536);
@@ -181,6 +195,13 @@ cudaError_t launch_features(const int64_t *ooff, const int32_t *ocol, const int3
                                                                          ctr);
     k_feat_final<<<(unsigned)ceil_div((int64_t)ns * 32, 256), 256, 0, s>>>(hist, seg_off, ns, n, feat);
     count_launches(m > 0 ? 2 : 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_best_level(const double *ari, int k, int nseg, int32_t *best, double *best_ari, cudaStream_t s) {
+    if (nseg <= 0) return cudaSuccess;
+    k_best_level<<<(unsigned)ceil_div(nseg, 128), 128, 0, s>>>(ari, k, nseg, best, best_ari);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -55,6 +55,52 @@ k_prune(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint
     }
 }
 
+// Per-graph thresholds: the edge's graph is the segment of its source row.
+template <bool HOOK>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_prune_seg(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t, int64_t n, int64_t m,
+            int measure, const int64_t *sp, const int64_t *sq, const int64_t *seg_off, int nseg, uint32_t *keep,
+            int32_t *parent, unsigned long long *ctr) {
+    __shared__ int ws[TILE_THREADS / 32];
+    if (graph_bad(ctr)) return;
+    const int64_t k0 = (int64_t)blockIdx.x * TILE;
+    const int64_t klast = min(k0 + TILE, m) - 1;
+    const int64_t r0 = row_search(ooff, 0, n - 1, k0);
+    const int64_t r1 = row_search(ooff, r0, n - 1, klast);
+    const unsigned lane = lane_id();
+    int kept = 0;
+    for (int i = 0; i < TILE_ITEMS; ++i) {
+        const int64_t jw = k0 + (int64_t)i * TILE_THREADS + (threadIdx.x & ~31u);
+        const int64_t j = jw + lane;
+        bool kp = false;
+        if (j < m) {
+            const int64_t u = row_search(ooff, r0, r1, j);
+            int lo = 0, hi = nseg - 1;               // segment of u
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (seg_off[mid] <= u) lo = mid; else hi = mid - 1;
+            }
+            const int32_t v = ocol[j];
+            const int64_t s = (int64_t)deg[u] + deg[v];
+            const int64_t p = sp[lo], q = sq[lo];
+            kp = q > 0 && (needs_wide_dev(p, q) ? keep_edge<true>(measure, t[j], s, p, q)
+                                                : keep_edge<false>(measure, t[j], s, p, q));
+            if (HOOK && kp) uf_link(parent, (int32_t)u, v, ctr);
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, kp);
+        if (lane == 0 && jw < m) keep[jw >> 5] = b;
+        kept += kp ? 1 : 0;
+    }
+    kept = warp_sum(kept);
+    if (lane == 0) ws[threadIdx.x >> 5] = kept;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < TILE_THREADS / 32; ++w) tot += ws[w];
+        if (tot) atomicAdd(&ctr[C_KEPT], (unsigned long long)tot);
+    }
+}
+
 // Number of neighbours greater than u in each row (the canonical edges the row owns).
 __global__ void k_upper_counts(const int64_t *off, const int32_t *col, int64_t n, int32_t *cnt) {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
@@ -130,6 +176,18 @@ cudaError_t launch_prune(const int64_t *ooff, const int32_t *ocol, const int32_t
         if (wide) k_prune<false, true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, a.measure, a.p, a.q, keep, parent, ctr);
         else k_prune<false, false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, a.measure, a.p, a.q, keep, parent, ctr);
     }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prune_seg(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
+                             int64_t n, int64_t m, int measure, const int64_t *sp, const int64_t *sq,
+                             const int64_t *seg_off, int nseg, bool hook, uint32_t *keep, int32_t *parent,
+                             unsigned long long *ctr, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)ceil_div(m, TILE);
+    if (hook) k_prune_seg<true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, measure, sp, sq, seg_off, nseg, keep, parent, ctr);
+    else k_prune_seg<false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, measure, sp, sq, seg_off, nseg, keep, parent, ctr);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -201,6 +201,14 @@ cudaError_t launch_forest_buckets(const int64_t *ooff, const int32_t *ocol, cons
     return cudaGetLastError();
 }
 
+cudaError_t launch_snapshot(int32_t *parent, int64_t n, int32_t *labels, const int64_t *seg_off, int nseg,
+                            unsigned long long *ncomp, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_snapshot<<<grid_for(n), 256, 0, s>>>(parent, n, labels, seg_off, nseg, ncomp);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sweep_level(const int32_t *fu, const int32_t *fv, const unsigned long long *bucket, int k, int L,
                                int64_t n, int32_t *parent, int32_t *labels, const int64_t *seg_off, int nseg,
                                unsigned long long *ncomp, unsigned long long *ctr, cudaStream_t s) {

@@ -112,6 +112,10 @@ struct PruneArgs {
 cudaError_t launch_prune(const int64_t *ooff, const int32_t *ocol, const int32_t *deg,
                          const uint32_t *t, int64_t n, int64_t m, PruneArgs a, uint32_t *keep,
                          int32_t *parent, unsigned long long *ctr, cudaStream_t s);
+cudaError_t launch_prune_seg(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
+                             int64_t n, int64_t m, int measure, const int64_t *sp, const int64_t *sq,
+                             const int64_t *seg_off, int nseg, bool hook, uint32_t *keep, int32_t *parent,
+                             unsigned long long *ctr, cudaStream_t s);
 cudaError_t launch_export(const int64_t *off, const int32_t *col, const int32_t *deg,
                           const int64_t *ooff, const int32_t *ocol, const uint32_t *t,
                           const uint32_t *keep, int64_t n, int64_t nnz, const int64_t *uoff,
@@ -135,11 +139,15 @@ cudaError_t launch_sweep_level(const int32_t *fu, const int32_t *fv, const unsig
                                int64_t n, int32_t *parent, int32_t *labels, const int64_t *seg_off, int nseg,
                                unsigned long long *ncomp, unsigned long long *ctr, cudaStream_t s);
 
+cudaError_t launch_snapshot(int32_t *parent, int64_t n, int32_t *labels, const int64_t *seg_off, int nseg,
+                            unsigned long long *ncomp, cudaStream_t s);
+
 // eval.cu: picker features per graph and adjusted Rand index per (level, graph).
 cudaError_t launch_features(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
                             int64_t n, int64_t m, const int64_t *seg_off, int nseg, unsigned int *hist, float *feat,
                             unsigned long long *ctr, cudaStream_t s);
 int ari_table_bits(int64_t n);
+cudaError_t launch_best_level(const double *ari, int k, int nseg, int32_t *best, double *best_ari, cudaStream_t s);
 cudaError_t launch_ari(const int32_t *labels, int k, const int32_t *truth, int64_t n, const int64_t *seg_off, int nseg,
                        unsigned int *bsz, unsigned int *size, unsigned long long *keys, unsigned int *cnt,
                        unsigned long long *sums, double *out, unsigned long long *ctr, cudaStream_t s);
@@ -189,6 +197,11 @@ __device__ __forceinline__ bool keep_edge(int measure, uint32_t tt, int64_t s, i
     const int64_t tw = 3 * (int64_t)tt + 2 - s;
     if (WIDE) return (__int128)tw * q >= (__int128)p;
     return tw * q >= p;
+}
+
+__device__ __forceinline__ bool needs_wide_dev(int64_t p, int64_t q) {
+    const int64_t lim = (int64_t)1 << 28;
+    return !(p > -lim && p < lim && q < lim);
 }
 
 inline bool needs_wide(int64_t p, int64_t q) {

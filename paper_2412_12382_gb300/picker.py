@@ -1,0 +1,108 @@
+"""Learned threshold picker: labelled data, training and inference.
+
+Orchestration of library calls only (every computation is a kernel of
+libtectonic.so): a batch of degree-corrected SBM graphs is built on the GPU,
+`tec_features` gives the 66 inputs per graph, `tec_sweep` the components at
+the 64 grid thresholds b/128, `tec_ari` their adjusted Rand index against the
+planted blocks, `tec_ari_best` the best level b*; the network regresses b*/64
+(`tec_picker_train`).  Inference: features -> `tec_picker_forward` ->
+`tec_picker_thresholds` -> `tec_prune_components_batch`.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+
+import numpy as np
+
+from . import tectonic as T
+
+K = 64
+DEN = 128
+GRID_P = list(range(1, K + 1))
+GRID_Q = [DEN] * K
+
+
+def label_batch(seeds, n_lo=1000, n_hi=100000, measure=T.TECTONIC):
+    """Features, best level (0-based), best ARI and the full ARI table (K x G)
+    for the DC-SBM graphs of `seeds` (CUDA tensors)."""
+    from graphgen.gpu import dcsbm_batch_gpu
+    off, col, seg, truth, specs = dcsbm_batch_gpu(seeds, n_lo, n_hi)
+    g = T.Graph(off, col)
+    feats = g.features(seg)
+    labels, _ = g.sweep(measure, GRID_P, GRID_Q, seg_off=seg, count=False)
+    ari = g.ari(labels, truth, seg)
+    best, best_ari = T.ari_best(ari)
+    g.free()
+    return {"feats": feats, "best": best, "best_ari": best_ari, "ari": ari, "n": [s.n for s in specs]}
+
+
+def build_dataset(seeds, n_lo=1000, n_hi=100000, batch=256, measure=T.TECTONIC):
+    import torch
+    parts = [label_batch(list(seeds[i:i + batch]), n_lo, n_hi, measure) for i in range(0, len(seeds), batch)]
+    out = {k: torch.cat([p[k] for p in parts], dim=1 if k == "ari" else 0) for k in ("feats", "best", "best_ari", "ari")}
+    out["target"] = (out["best"].to(torch.float32) + 1.0) / K
+    return out
+
+
+def fixed_level(dataset) -> int:
+    """The single grid level of highest mean ARI over a dataset (0-based):
+    the method with one global threshold, as in the paper."""
+    return int(dataset["ari"].mean(dim=1).argmax().item())
+
+
+def init_params(seed: int = 0):
+    """Kaiming-uniform weights (bound sqrt(6 / fan_in)), zero biases, float32."""
+    rng = np.random.default_rng(seed)
+    IN, H = 66, 128
+    parts = [rng.uniform(-np.sqrt(6 / IN), np.sqrt(6 / IN), H * IN), np.zeros(H),
+             rng.uniform(-np.sqrt(6 / H), np.sqrt(6 / H), H * H), np.zeros(H),
+             rng.uniform(-np.sqrt(6 / H), np.sqrt(6 / H), H), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def train(dataset, epochs=300, batch=256, lr=1e-3, seed=0):
+    picker = T.Picker(init_params(seed))
+    losses = picker.train(dataset["feats"], dataset["target"], epochs, batch, lr, seed)
+    return picker, losses
+
+
+def predict_levels(picker, feats, bf16=False):
+    """0-based grid level per graph."""
+    p, _ = T.picker_thresholds(picker.forward(feats, bf16))
+    return p - 1
+
+
+def evaluate(picker, dataset, bf16=False, baseline_level=None):
+    """ARI lost against the best grid threshold, per graph, for the picker and
+    (optionally) one fixed level."""
+    import torch
+    lv = predict_levels(picker, dataset["feats"], bf16).long()
+    cols = torch.arange(lv.numel(), device=lv.device)
+    got = dataset["ari"][lv, cols]
+    loss = (dataset["best_ari"] - got).cpu().numpy()
+    out = {"mean_dARI": float(loss.mean()), "p95_dARI": float(np.percentile(loss, 95)), "max_dARI": float(loss.max()),
+           "mean_ARI": float(got.mean().item()), "mean_best_ARI": float(dataset["best_ari"].mean().item())}
+    if baseline_level is not None:
+        fixed = dataset["ari"][baseline_level]
+        out["fixed_level"] = int(baseline_level) + 1
+        out["fixed_mean_ARI"] = float(fixed.mean().item())
+        out["fixed_mean_dARI"] = float((dataset["best_ari"] - fixed).mean().item())
+    return out
+
+
+def save(picker, path, meta=None):
+    params, m, v, step = picker.get_params(with_adam=True)
+    digest = hashlib.sha256(params.tobytes() + m.tobytes() + v.tobytes()).hexdigest()
+    np.savez(path, params=params, adam_m=m, adam_v=v, step=np.int64(step),
+             meta=json.dumps(meta or {}), sha256=digest)
+
+
+def load(path):
+    d = np.load(path, allow_pickle=False)
+    params, m, v = d["params"], d["adam_m"], d["adam_v"]
+    if hashlib.sha256(params.tobytes() + m.tobytes() + v.tobytes()).hexdigest() != str(d["sha256"]):
+        raise ValueError(f"checkpoint {path} fails its checksum")
+    picker = T.Picker(params)
+    picker.set_params(params, m, v, int(d["step"]))
+    return picker, json.loads(str(d["meta"]))

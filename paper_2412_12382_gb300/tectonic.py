@@ -60,6 +60,18 @@ SIGNATURES = {
     "tec_sweep": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P], ctypes.c_int),
     "tec_features": ([_P, _P, ctypes.c_int, _P], ctypes.c_int),
     "tec_ari": ([_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "tec_ari_best": ([_P, ctypes.c_int, ctypes.c_int, _P, _P, _P], ctypes.c_int),
+    "tec_prune_components_batch": ([_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, _P], ctypes.c_int),
+    "tec_picker_create": ([_P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "tec_picker_free": ([_P], ctypes.c_int),
+    "tec_picker_get_params": ([_P, _P, _P, _P, _PI64], ctypes.c_int),
+    "tec_picker_set_params": ([_P, _P, _P, _P, _I64], ctypes.c_int),
+    "tec_picker_forward": ([_P, _P, _I64, ctypes.c_int, _P], ctypes.c_int),
+    "tec_picker_loss_grad": ([_P, _P, _P, _I64, _P, _P], ctypes.c_int),
+    "tec_picker_adam_step": ([_P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float], ctypes.c_int),
+    "tec_picker_train": ([_P, _P, _P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64, _P],
+                         ctypes.c_int),
+    "tec_picker_thresholds": ([_P, _I64, _P, _P, _P], ctypes.c_int),
     "tec_components_noalloc": ([_I64, _I64, _P, _P, _P, _P, _PI64, _P], ctypes.c_int),
 }
 
@@ -303,6 +315,17 @@ class Graph:
                                 _ptr(seg_off) if seg_off is not None else None, nseg, _ptr(out)))
         return out
 
+    def prune_components_batch(self, measure: int, p, q, seg_off, labels=None, count: bool = True):
+        """Per-graph thresholds p[s]/q[s] (CUDA int64): local labels (n) and components per graph."""
+        torch = _torch()
+        nseg = seg_off.numel() - 1
+        if labels is None:
+            labels = self._empty(self.n, torch.int32)
+        nc = np.empty(nseg, dtype=np.int64)
+        check(self._lib.tec_prune_components_batch(self._h, int(measure), _ptr(p), _ptr(q), _ptr(seg_off), nseg,
+                                                   _ptr(labels), _ptr(nc) if count else None))
+        return labels, (nc if count else None)
+
     def full_pass(self, measure: int, p: int, q: int, labels=None, count: bool = True):
         torch = _torch()
         if labels is None:
@@ -326,3 +349,87 @@ class Graph:
         check(self._lib.tec_graph_info(self._h, ctypes.byref(n_), ctypes.byref(m_)))
         self.n, self.m = n_.value, m_.value
         return labels, nc.value
+
+
+PICKER_PARAMS = 25217
+
+
+def ari_best(ari, stream=None):
+    """Row of highest ARI per graph (first on ties) and its value: (int32, float64) CUDA tensors."""
+    torch = _require_cuda()
+    k, nseg = ari.shape
+    best = torch.empty(nseg, dtype=torch.int32, device="cuda")
+    val = torch.empty(nseg, dtype=torch.float64, device="cuda")
+    stream = stream or torch.cuda.current_stream()
+    check(load_library().tec_ari_best(_ptr(ari.contiguous()), k, nseg, _ptr(best), _ptr(val), _P(stream.cuda_stream)))
+    return best, val
+
+
+def picker_thresholds(y, stream=None):
+    """Grid thresholds (p, q) as CUDA int64 tensors from picker outputs y."""
+    torch = _require_cuda()
+    n = y.numel()
+    p = torch.empty(n, dtype=torch.int64, device="cuda")
+    q = torch.empty(n, dtype=torch.int64, device="cuda")
+    stream = stream or torch.cuda.current_stream()
+    check(load_library().tec_picker_thresholds(_ptr(y.contiguous()), n, _ptr(p), _ptr(q), _P(stream.cuda_stream)))
+    return p, q
+
+
+class Picker:
+    """The learned threshold picker (a ``tec_picker``)."""
+
+    def __init__(self, init_params=None, stream=None):
+        torch = _require_cuda()
+        self._lib = load_library()
+        self.stream = stream or torch.cuda.current_stream()
+        self._h = _P()
+        init = None if init_params is None else np.ascontiguousarray(init_params, dtype=np.float32)
+        check(self._lib.tec_picker_create(_ptr(init), _P(self.stream.cuda_stream), ctypes.byref(self._h)))
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            check(self._lib.tec_picker_free(self._h))
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def get_params(self, with_adam: bool = False):
+        p = np.empty(PICKER_PARAMS, dtype=np.float32)
+        m = np.empty_like(p) if with_adam else None
+        v = np.empty_like(p) if with_adam else None
+        step = ctypes.c_int64(0)
+        check(self._lib.tec_picker_get_params(self._h, _ptr(p), _ptr(m), _ptr(v), ctypes.byref(step)))
+        return (p, m, v, step.value) if with_adam else p
+
+    def set_params(self, params, m=None, v=None, step: int = 0):
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in (params, m, v)]
+        check(self._lib.tec_picker_set_params(self._h, *[_ptr(a) for a in arrs], int(step)))
+
+    def forward(self, feats, bf16: bool = False):
+        torch = _torch()
+        out = torch.empty(feats.shape[0], dtype=torch.float32, device="cuda")
+        check(self._lib.tec_picker_forward(self._h, _ptr(feats.contiguous()), feats.shape[0], int(bf16), _ptr(out)))
+        return out
+
+    def loss_grad(self, feats, target):
+        torch = _torch()
+        g = torch.empty(PICKER_PARAMS, dtype=torch.float32, device="cuda")
+        loss = ctypes.c_float(0.0)
+        check(self._lib.tec_picker_loss_grad(self._h, _ptr(feats.contiguous()), _ptr(target.contiguous()),
+                                             feats.shape[0], ctypes.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def adam_step(self, grad=None, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        check(self._lib.tec_picker_adam_step(self._h, _ptr(grad), lr, beta1, beta2, eps))
+
+    def train(self, feats, target, epochs: int, batch: int = 256, lr: float = 1e-3, seed: int = 0):
+        losses = np.empty(max(epochs, 1), dtype=np.float32)
+        check(self._lib.tec_picker_train(self._h, _ptr(feats.contiguous()), _ptr(target.contiguous()),
+                                         feats.shape[0], int(epochs), int(batch), float(lr), int(seed),
+                                         _ptr(losses)))
+        return losses[:epochs]

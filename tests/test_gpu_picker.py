@@ -1,0 +1,119 @@
+"""Learned threshold picker: kernels against the float64 oracle, per-graph
+thresholds against the oracle's passes, and what training gains."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp as M
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tec(cuda_device):
+    import paper_2412_12382_gb300 as pkg
+    from paper_2412_12382_gb300 import build
+    build.build()
+    pkg.load_library()
+    return pkg
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, 66)).astype(np.float32)
+    X[:, 64:] = rng.uniform(2, 12, size=(n, 2))
+    return X, rng.uniform(0, 1, n).astype(np.float32)
+
+
+def test_forward_and_gradient_against_oracle(tec):
+    import torch
+    from paper_2412_12382_gb300.tectonic import Picker
+    X, t = _data(200, 1)
+    theta = M.init(4).astype(np.float32)
+    theta[-1] = 0.3
+    pk = Picker(theta)
+    Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    y = pk.forward(Xd).cpu().numpy()
+    yo, _ = M.forward(theta.astype(np.float64), X.astype(np.float64))
+    np.testing.assert_allclose(y, yo, rtol=1e-4, atol=1e-5)
+    loss, g = pk.loss_grad(Xd, td)
+    lo, go = M.loss_and_grad(theta.astype(np.float64), X.astype(np.float64), t.astype(np.float64))
+    g = g.cpu().numpy()
+    assert abs(loss - lo) <= 1e-4 * abs(lo)
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go)
+    big = np.abs(go) > 1e-3 * np.abs(go).max()
+    np.testing.assert_allclose(g[big], go[big], rtol=1e-3)
+    # bf16 inference: close to float32
+    yb = pk.forward(Xd, bf16=True).cpu().numpy()
+    assert np.max(np.abs(yb - y)) <= 0.05 * (np.abs(y).max() + 1)
+    pk.free()
+
+
+def test_adam_step_against_oracle(tec):
+    import torch
+    from paper_2412_12382_gb300.tectonic import Picker
+    X, t = _data(64, 2)
+    theta = M.init(5).astype(np.float32)
+    pk = Picker(theta)
+    m = np.zeros(M.NPARAM)
+    v = np.zeros(M.NPARAM)
+    th = theta.astype(np.float64)
+    for step in range(1, 4):
+        _, g = pk.loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda())
+        gh = g.cpu().numpy().astype(np.float64)
+        pk.adam_step(g, lr=1e-2)
+        th, m, v = M.adam(th, gh, m, v, step, lr=1e-2)
+        np.testing.assert_allclose(pk.get_params(), th, rtol=1e-5, atol=1e-6)
+    pk.free()
+
+
+def test_training_fits_and_checkpoint_round_trip(tec, tmp_path):
+    import torch
+    from paper_2412_12382_gb300 import picker as P
+    from paper_2412_12382_gb300.tectonic import Picker
+    rng = np.random.default_rng(3)
+    X = rng.uniform(0, 1, (1000, 66)).astype(np.float32)
+    t = (0.3 * X[:, 0] + 0.5 * X[:, 1] * X[:, 2]).astype(np.float32)
+    pk = Picker(P.init_params(1))
+    losses = pk.train(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda(), epochs=60, batch=128, lr=2e-3, seed=7)
+    assert losses[-1] < 0.05 * losses[0]
+    path = str(tmp_path / "pk.npz")
+    P.save(pk, path, {"note": "test"})
+    pk2, meta = P.load(path)
+    Xd = torch.from_numpy(X[:50]).cuda()
+    assert torch.equal(pk.forward(Xd), pk2.forward(Xd)) and meta["note"] == "test"
+    pk.free()
+    pk2.free()
+
+
+def test_per_graph_thresholds_match_oracle(tec):
+    import torch
+    from graphgen.batch import disjoint_union
+    from graphgen.dcsbm import dcsbm_csr
+    graphs = [dcsbm_csr(s, 1000, 3000)[:2] for s in (20000, 20001, 20002)]
+    off, col, seg = disjoint_union(graphs)
+    g = tec.Graph(torch.from_numpy(off).cuda(), torch.from_numpy(col).cuda())
+    ps, qs = [3, 9, 20], [128, 128, 128]
+    lab, nc = g.prune_components_batch(tec.TECTONIC, torch.tensor(ps).cuda(), torch.tensor(qs).cuda(),
+                                       torch.from_numpy(seg).cuda())
+    lab = lab.cpu().numpy()
+    for i, (go, gc) in enumerate(graphs):
+        r = O.full_pass(go, gc, O.TECTONIC, ps[i], qs[i])
+        assert nc[i] == r.ncomp and np.array_equal(lab[seg[i]:seg[i + 1]], r.labels)
+    g.free()
+
+
+def test_picker_gains_over_one_fixed_threshold(tec):
+    # trained on 768 DC-SBM graphs (seeds 10000+), judged on 128 held-out
+    # graphs (seeds 20000+) by the ARI lost against each graph's best grid
+    # threshold; the method without a picker uses one global threshold (the
+    # grid level of best mean training ARI)
+    from paper_2412_12382_gb300 import picker as P
+    train = P.build_dataset(list(range(10000, 10768)), 1000, 4000)
+    held = P.build_dataset(list(range(20000, 20128)), 1000, 4000)
+    pk, losses = P.train(train, epochs=300, batch=128, lr=1e-3, seed=0)
+    res = P.evaluate(pk, held, baseline_level=P.fixed_level(train))
+    print("picker evaluation:", res)
+    assert losses[-1] < losses[0]
+    assert res["mean_dARI"] < res["fixed_mean_dARI"]
+    pk.free()

@@ -195,6 +195,95 @@ def oracle_sample_rate(off_h, col_h, p, q, target_s=12.0, seed=0):
     return total_e / total_t, total_e, threads, total_t
 
 
+def _timed(fn, stream, reps):
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    out = None
+    for a, b in ev:
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ev), out
+
+
+def bench_batched_sweep(reps=3):
+    """256 degree-corrected SBM graphs (seeds 1000-1255, n log-uniform in
+    [1000, 200000]) as one batch: components at the 64 thresholds b/128 by the
+    spanning-forest sweep, against 64 independent prune + components passes."""
+    import torch
+    from graphgen.gpu import dcsbm_batch_gpu
+    from paper_2412_12382_gb300 import TECTONIC, Graph
+    from paper_2412_12382_gb300 import picker as PK
+    t0 = time.time()
+    off, col, seg, truth, specs = dcsbm_batch_gpu(list(range(1000, 1256)), 1000, 200000)
+    gen_s = time.time() - t0
+    g = Graph(off, col)
+    stream = g.stream
+    sup_ms, _ = _timed(lambda: g.support(), stream, 2)
+    nseg = seg.numel() - 1
+    sweep_ms, _ = _timed(lambda: g.sweep(TECTONIC, PK.GRID_P, PK.GRID_Q, seg_off=seg, count=False), stream,
+                         reps + 1)
+    thr = [(torch.full((nseg,), b, dtype=torch.int64, device="cuda"),
+            torch.full((nseg,), 128, dtype=torch.int64, device="cuda")) for b in PK.GRID_P]
+    lab = torch.empty(g.n, dtype=torch.int32, device="cuda")
+
+    def independent():
+        for p, q in thr:
+            g.prune_components_batch(TECTONIC, p, q, seg, labels=lab, count=False)
+
+    ind_ms, _ = _timed(independent, stream, reps)
+    m = g.m
+    g.free()
+    return {"workload": "256 DC-SBM graphs, seeds 1000-1255, n log-uniform in [1e3, 2e5], 64 thresholds b/128",
+            "graphs": nseg, "n": int(off.numel() - 1), "m": int(m), "support_ms": sup_ms,
+            "sweep_ms": sweep_ms, "independent_passes_ms": ind_ms, "speedup_vs_independent": ind_ms / sweep_ms,
+            "graphs_per_s": nseg / (sweep_ms / 1e3), "edges_per_s": m / (sweep_ms / 1e3),
+            "input_generation_s": gen_s}
+
+
+def bench_picker(reps=3):
+    """Held-out DC-SBM graphs (seeds 20000-20499, n in [1000, 100000]) as one
+    batch.  Picker path: features, bf16 network, grid thresholds, one batched
+    prune + components.  Sweep path: 64-threshold sweep, 64 ARI evaluations,
+    best level.  The triangle counts, shared by both, are timed apart."""
+    import numpy as np
+    import torch
+    from graphgen.gpu import dcsbm_batch_gpu
+    from paper_2412_12382_gb300 import TECTONIC, Graph
+    from paper_2412_12382_gb300 import picker as PK
+    from paper_2412_12382_gb300 import tectonic as T
+    ckpt = os.path.join(ROOT, "paper_2412_12382_gb300", "picker_weights.npz")
+    pk, meta = PK.load(ckpt)
+    off, col, seg, truth, specs = dcsbm_batch_gpu(list(range(20000, 20500)), 1000, 100000)
+    g = Graph(off, col)
+    stream = g.stream
+    sup_ms, _ = _timed(lambda: g.support(), stream, 2)
+
+    def picker_path():
+        y = pk.forward(g.features(seg), bf16=True)
+        p, q = T.picker_thresholds(y)
+        return g.prune_components_batch(TECTONIC, p, q, seg, count=False)[0]
+
+    def sweep_path():
+        labels, _ = g.sweep(TECTONIC, PK.GRID_P, PK.GRID_Q, seg_off=seg, count=False)
+        ari = g.ari(labels, truth, seg)
+        return T.ari_best(ari)
+
+    picker_ms, plab = _timed(picker_path, stream, reps + 1)
+    sweep_ms, (best, best_ari) = _timed(sweep_path, stream, reps + 1)
+    got = g.ari(plab[None, :], truth, seg)[0]
+    d = (best_ari - got).cpu().numpy()
+    g.free()
+    pk.free()
+    return {"workload": "500 held-out DC-SBM graphs, seeds 20000-20499, n log-uniform in [1e3, 1e5]",
+            "graphs": int(seg.numel() - 1), "picker_ms": picker_ms, "sweep_ms": sweep_ms,
+            "ratio_sweep_over_picker": sweep_ms / picker_ms, "support_ms": sup_ms,
+            "ratio_including_support": (sweep_ms + sup_ms) / (picker_ms + sup_ms),
+            "mean_dARI": float(d.mean()), "p95_dARI": float(np.percentile(d, 95)), "max_dARI": float(d.max()),
+            "inference": "bf16", "trained_on": meta.get("train_seeds"), "epochs_kept": meta.get("epochs_kept")}
+
+
 def run_reference(args, spec, rank, world):
     import numpy as np
     import torch
@@ -241,6 +330,8 @@ def main():
     ap.add_argument("--workload", default="rmat26", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the batched sweep measurement")
+    ap.add_argument("--no-picker", action="store_true", help="skip the picker-vs-sweep measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warning: fewer than 3 warm-up steps")
@@ -367,6 +458,17 @@ def main():
                          f"+ exact prune, {tt:.1f} s on {thr} host threads; components not included"}
         del off_np, col_np
 
+    g.free()
+    del off, col, labels
+    torch.cuda.empty_cache()
+    sweep = picker = None
+    if rank == 0 and not args.no_sweep:
+        sweep = bench_batched_sweep()
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_picker:
+        picker = bench_picker()
+        torch.cuda.empty_cache()
+
     if rank == 0:
         clocks = clk.summary()
         line = {
@@ -390,9 +492,9 @@ def main():
                          "traffic_source": TRAFFIC_CAPTURE["source"] if traffic else None},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "gpu_launches_per_step": launches / args.steps, "clocks": clocks,
+            "batched_sweep": sweep, "picker_vs_sweep": picker,
         }
         print(json.dumps(line), flush=True)
-    g.free()
     if dist is not None:
         dist.destroy_process_group()
     return 0

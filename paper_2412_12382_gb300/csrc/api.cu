@@ -65,7 +65,7 @@ void free_graph_memory(tec_graph *g) {
     void *ptrs[] = {g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->parent, g->tasks,
                     g->flags, g->tile_cnt, g->tile_base, g->bsum, g->uoff, g->ucnt, g->labels, g->lvl, g->best,
                     g->fu, g->fv, g->bucket, g->thr, g->sw_ncomp, g->seg_hist, g->ari_sums,
-                    g->ari_size, g->ari_keys, g->ari_cnt, g->ctr};
+                    g->ari_size, g->ari_keys, g->ari_cnt, g->msf_u, g->msf_v, g->msf_k, g->msf_cnt, g->ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (g->ctr_host) cudaFreeHost(g->ctr_host);
@@ -174,7 +174,7 @@ tec_status ensure_seg_scratch(tec_graph *g, int ns) {
     g->ari_sums = nullptr;
     g->seg_cap = 0;
     TEC_TRY(dalloc(&g->seg_hist, (int64_t)ns * 64, "per-graph histograms"));
-    TEC_TRY(dalloc(&g->ari_sums, (int64_t)ns * 3, "per-graph pair sums"));
+    TEC_TRY(dalloc(&g->ari_sums, (int64_t)ns * 2 * ARI_CHUNK, "per-graph pair sums"));
     g->seg_cap = ns;
     return TEC_OK;
 }
@@ -208,14 +208,17 @@ tec_status tec_ari(tec_graph *g, int k, const int32_t *labels, const int32_t *tr
     DeviceGuard dg(g->device);
     const int ns = seg_off ? nseg : 1;
     TEC_TRY(ensure_seg_scratch(g, ns));
-    if (!g->ari_size) TEC_TRY(dalloc(&g->ari_size, g->n_cap, "component sizes"));
-    if (!g->ari_keys) {
-        const int64_t tsize = (int64_t)1 << ari_table_bits(g->n_cap);
+    const int64_t tsize = (int64_t)1 << ari_table_bits(g->n_cap);
+    if (!g->ari_size) {
+        TEC_TRY(dalloc(&g->ari_size, 2 * std::max<int64_t>(g->n_cap, 1), "component sizes"));
         TEC_TRY(dalloc(&g->ari_keys, tsize, "cell keys"));
         TEC_TRY(dalloc(&g->ari_cnt, tsize, "cell counts"));
+        g->ari_tag = ~0ull;                      // forces the first zeroing
     }
-    TEC_CUDA(launch_ari(labels, k, truth, g->n, seg_off, nseg, g->seg_hist, g->ari_size, g->ari_keys, g->ari_cnt,
-                        g->ari_sums, ari_out, g->ctr, g->stream));
+    if (g->ari_n != g->n) g->ari_tag = ~0ull;   // size counters beyond the old n may be stale
+    g->ari_n = g->n;
+    TEC_CUDA(launch_ari(labels, k, truth, g->n, seg_off, nseg, g->seg_hist, g->ari_size, std::max<int64_t>(g->n_cap, 1),
+                        g->ari_keys, g->ari_cnt, tsize, g->ari_sums, ari_out, &g->ari_tag, g->ctr, g->stream));
     return TEC_OK;
 }
 
@@ -571,29 +574,59 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
         g->sw_ncomp_cap = (int64_t)k * nsl;
     }
     cudaStream_t s = g->stream;
+    // live-edge list of the later Boruvka rounds (16 bytes per edge); without
+    // the memory for it those rounds rescan the CSR instead
+    if (g->msf_cap == 0 && g->m_cap > 0) {
+        const int64_t tiles = ceil_div(g->m_cap, (int64_t)TILE), cap = tiles * TILE;
+        if (dalloc(&g->msf_u, cap, "live edges") != TEC_OK || dalloc(&g->msf_v, cap, "live edges") != TEC_OK ||
+            dalloc(&g->msf_k, cap, "live edge keys") != TEC_OK || dalloc(&g->msf_cnt, tiles, "live edge counts") != TEC_OK) {
+            void *part[] = {g->msf_u, g->msf_v, g->msf_k, g->msf_cnt};
+            for (void *q2 : part)
+                if (q2) cudaFree(q2);
+            g->msf_u = g->msf_v = g->msf_cnt = nullptr;
+            g->msf_k = nullptr;
+            g->msf_cap = -1;
+            clear_error();
+        } else {
+            g->msf_cap = cap;
+        }
+    }
+    const bool list = g->msf_cap > 0;
+    int32_t *lu = list ? g->msf_u : nullptr, *lv = list ? g->msf_v : nullptr, *lc = list ? g->msf_cnt : nullptr;
+    unsigned long long *lk = list ? g->msf_k : nullptr;
     TEC_CUDA(cudaMemcpyAsync(g->thr, hthr.data(), hthr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     TEC_TRY(ensure_support(g));
-    TEC_CUDA(launch_levels(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, (int)measure, g->thr, g->thr + k, k, wide,
-                           g->lvl, g->ctr, s));
-    // Boruvka rounds of the maximum spanning forest
+    // Boruvka rounds of the maximum spanning forest; the first runs in the level pass
     g->pruned = g->hooked = false;
     TEC_CUDA(launch_cc_init(g->parent, g->n, s));
     if (g->n > 0) TEC_CUDA(cudaMemsetAsync(g->best, 0, (size_t)g->n * sizeof(unsigned long long), s));
+    TEC_CUDA(launch_levels(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, (int)measure, g->thr, g->thr + k, k, wide,
+                           g->lvl, g->best, lu, lv, lk, lc, g->ctr, s));
     int round = 0;
     for (; round < 64; ++round) {
         TEC_TRY(reset_counter(g, C_CHANGED));
-        TEC_CUDA(launch_msf_round(g->ooff, g->ocol, g->lvl, g->n, g->m, g->parent, g->best, g->ctr, s));
+        if (round > 0)
+            TEC_CUDA(launch_msf_offer(g->ooff, g->ocol, g->lvl, g->n, g->m, g->parent, g->best, lu, lv, lk, lc,
+                                      g->ctr, s));
+        TEC_CUDA(launch_msf_hook(g->ooff, g->ocol, g->lvl, g->n, g->parent, g->best, g->ctr, s));
         TEC_TRY(read_counters(g));
         if (g->ctr_host[C_CHANGED] == 0) break;
     }
     if (round == 64) return set_error(TEC_ETIMEOUT, "the spanning forest did not converge in 64 rounds");
     // offline sweep over the forest edges, highest level first
     TEC_CUDA(launch_forest_buckets(g->ooff, g->ocol, g->lvl, g->n, g->m, k, g->bucket, g->fu, g->fv, s));
+    std::vector<unsigned long long> boff((size_t)k + 2);   // bucket offsets, sized launches per level
+    TEC_CUDA(cudaMemcpyAsync(boff.data(), g->bucket + k + 1, boff.size() * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, s));
     TEC_CUDA(launch_cc_init(g->parent, g->n, s));
     TEC_CUDA(cudaMemsetAsync(g->sw_ncomp, 0, (size_t)k * nsl * sizeof(unsigned long long), s));
+    TEC_CUDA(cudaStreamSynchronize(s));
+    if (boff[k + 1] > (unsigned long long)std::max<int64_t>(g->n - 1, 0))
+        return set_error(TEC_EBADGRAPH, "spanning forest has %llu edges for %lld vertices", boff[k + 1],
+                         (long long)g->n);
     for (int L = k; L >= 1; --L) {
         const int dst = order[L - 1];
-        TEC_CUDA(launch_sweep_level(g->fu, g->fv, g->bucket, k, L, g->n, g->parent,
+        TEC_CUDA(launch_sweep_level(g->fu, g->fv, (int64_t)boff[L], (int64_t)boff[L + 1], g->n, g->parent,
                                     labels_out + (int64_t)dst * g->n, seg_off, nseg,
                                     g->sw_ncomp + (int64_t)dst * nsl, g->ctr, s));
     }

@@ -11,9 +11,20 @@
 //   C(size, 2), S_b = sum over blocks of C(size, 2), T = C(n, 2),
 //   ARI = (2 T S_ab - 2 S_a S_b) / (T (S_a + S_b) - 2 S_a S_b),
 // with ARI = 1 when the denominator is 0 (both partitions all singletons or
-// both one cluster) or n < 2.  Cell counts come from a device hash table
-// keyed by (component root, block); all sums are exact 64-bit integers and
-// the ratio is formed from exact 128-bit numerator and denominator.
+// both one cluster) or n < 2.  All sums are exact 64-bit integers and the
+// ratio is formed from exact 128-bit numerator and denominator.
+//
+// Per level, two passes over the vertices.  Sizes: each component's size is
+// a counter at its root.  Cells: each (component root, block) pair of a
+// component with at least two vertices is a counter in an open-addressing
+// hash table (singleton components add nothing to either sum).  The sums
+// are built incrementally: adding c to a counter that held o raises
+// C(count, 2) by o c + C(c, 2), so no pass over the counters is needed.
+// Lanes of a warp with the same root or cell add once for all of them.
+// Cell counters and keys carry the level's tag in their top 24 bits; a word
+// with an older tag reads as empty, so the table is zeroed only when the tag
+// wraps, not per level.  Sizes use two plain counter arrays in turn: each
+// level's first pass zeroes the array the next level will use.
 #include "tec_internal.cuh"
 
 namespace tec {
@@ -81,65 +92,250 @@ __global__ void k_feat_final(const unsigned int *hist, const int64_t *seg_off, i
 
 // ---------------------------------------------------------------- ARI
 
-constexpr unsigned long long EMPTY = ~0ull;
+constexpr int TAG_SHIFT = 40;
+constexpr unsigned long long CNT_MASK = (1ull << TAG_SHIFT) - 1ull;
+constexpr unsigned long long TAG_LIMIT = (1ull << (64 - TAG_SHIFT)) - 1ull;
+constexpr int BS_CHUNK = 8192;                   // vertices per block in k_block_sizes
 
 __device__ __forceinline__ uint64_t hkey(uint64_t key, int bits) {
     return (key * 0x9E3779B97F4A7C15ull) >> (64 - bits);
 }
 
-__global__ void k_block_sizes(const int32_t *truth, int64_t n, const int64_t *seg_off, int nseg, unsigned int *bsz,
-                              unsigned long long *ctr) {
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
-        const int b = truth[x];
-        if (b < 0 || b >= NBINS) { flag_status(ctr, ST_BADGRAPH); continue; }
-        const int s = seg_off ? seg_of(seg_off, nseg, x) : 0;
-        atomicAdd(&bsz[(int64_t)s * NBINS + b], 1u);
-    }
-}
-
-// Component sizes and (root, block) cell counts of one level.
-__global__ void k_ari_cells(const int32_t *labels, const int32_t *truth, int64_t n, const int64_t *seg_off, int nseg,
-                            unsigned int *size, unsigned long long *keys, unsigned int *cnt, int bits,
-                            unsigned long long *ctr) {
-    const uint64_t mask = (1ull << bits) - 1ull;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
-        const int b = truth[x];
-        if (b < 0 || b >= NBINS) continue;       // reported by k_block_sizes
-        const int64_t base = seg_off ? seg_off[seg_of(seg_off, nseg, x)] : 0;
-        const int64_t root = base + labels[x];
-        if (root < 0 || root >= n) { flag_status(ctr, ST_BADGRAPH); continue; }
-        atomicAdd(&size[root], 1u);
-        const uint64_t key = ((uint64_t)root << 6) | (uint64_t)b;
-        uint64_t h = hkey(key, bits);
-        for (uint64_t probe = 0; probe <= mask; ++probe) {
-            const unsigned long long old = atomicCAS(&keys[h], EMPTY, (unsigned long long)key);
-            if (old == EMPTY || old == key) {
-                atomicAdd(&cnt[h], 1u);
-                break;
-            }
-            h = (h + 1) & mask;
-        }
-    }
-}
-
 __device__ __forceinline__ unsigned long long c2(unsigned long long x) { return x * (x - (x > 0)) / 2; }
 
-// sums[3 s + 0] = S_ab, sums[3 s + 1] = S_a of segment s.
-__global__ void k_ari_reduce(const unsigned long long *keys, const unsigned int *cnt, int64_t tsize,
-                             const unsigned int *size, int64_t n, const int64_t *seg_off, int nseg,
-                             unsigned long long *sums) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tsize; i += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned int c = cnt[i];
-        if (c > 1) {
-            const int64_t root = (int64_t)(keys[i] >> 6);
-            const int s = seg_off ? seg_of(seg_off, nseg, root) : 0;
-            atomicAdd(&sums[3 * s], c2(c));
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Adds c to a level-tagged counter and returns the count it held at this
+// level (0 if the word carried an older tag).  Within a level a word only
+// goes from an older tag to the current one (by the compare-and-swap here)
+// and then grows, so a failed swap always leaves a current word and the
+// second iteration adds.
+__device__ __forceinline__ unsigned long long tagged_add(unsigned long long *w, unsigned long long tag,
+                                                         unsigned long long c) {
+    unsigned long long cur = __ldcg(w);
+    for (int it = 0; it < 2; ++it) {
+        if ((cur >> TAG_SHIFT) == tag) break;
+        const unsigned long long old = atomicCAS(w, cur, (tag << TAG_SHIFT) | c);
+        if (old == cur) return 0ull;
+        cur = old;
+    }
+    return atomicAdd(w, c) & CNT_MASK;
+}
+
+// Slot of cell key ck (< 2^40) at this level: linear probing from its hash,
+// claiming the first slot with an older tag.  Slots of this level are never
+// re-claimed, so a key is found wherever its first claim put it.  -1 if the
+// table is full (it holds 2n slots and at most n cells per level).
+__device__ __forceinline__ int64_t cell_slot(unsigned long long *keys, int bits, unsigned long long tag,
+                                             unsigned long long ck) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    const unsigned long long want = (tag << TAG_SHIFT) | ck;
+    uint64_t h = hkey(ck, bits);
+    for (uint64_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+        unsigned long long cur = __ldcg(&keys[h]);
+        for (int it = 0; it < 2; ++it) {         // a failed claim leaves a key of this level
+            if (cur == want) return (int64_t)h;
+            if ((cur >> TAG_SHIFT) == tag) break;
+            const unsigned long long old = atomicCAS(&keys[h], cur, want);
+            if (old == cur) return (int64_t)h;
+            cur = old;
         }
-        if (i < n && size[i] > 1) {
-            const int s = seg_off ? seg_of(seg_off, nseg, i) : 0;
-            atomicAdd(&sums[3 * s + 1], c2(size[i]));
+        if (cur == want) return (int64_t)h;
+    }
+    return -1;
+}
+
+// Groups the valid lanes of a warp by key for one atomic per group: returns
+// a mask of lanes that hold this lane's key (the lane itself at least).  Any
+// grouping by equal keys is exact, because every group computes its pair
+// increment from the count its own atomic returns; so the full (slow) match
+// runs only when neighbouring lanes repeat keys often.  All keys equal
+// (a large component over consecutive vertices) costs one shuffle; mostly
+// distinct keys (singletons, interleaved components) add lane by lane.
+template <typename K>
+__device__ __forceinline__ unsigned key_group(bool valid, K key) {
+    const unsigned lane = lane_id();
+    const unsigned vm = __ballot_sync(0xffffffffu, valid);
+    if (!vm) return 0u;
+    const K k0 = __shfl_sync(0xffffffffu, key, __ffs(vm) - 1);
+    if (__all_sync(0xffffffffu, !valid || key == k0)) return vm;
+    const K up = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool rep = valid && lane > 0 && ((vm >> (lane - 1)) & 1u) && key == up;
+    if (__popc(__ballot_sync(0xffffffffu, rep)) >= 8) return __match_any_sync(0xffffffffu, key) & vm;
+    return 1u << lane;
+}
+
+// Adds the per-lane pair-count increments of a warp to sums[2 s + which]:
+// one atomic per warp when every valid lane is in the same segment.
+__device__ __forceinline__ void add_pairs(unsigned long long *sums, int which, int s, bool valid,
+                                          unsigned long long d) {
+    const int s0 = __shfl_sync(0xffffffffu, s, 0);
+    if (__all_sync(0xffffffffu, !valid || s == s0)) {
+        d = warp_sum64(d);
+        if (lane_id() == 0 && d) atomicAdd(&sums[2 * s0 + which], d);
+    } else if (d) {
+        atomicAdd(&sums[2 * s + which], d);
+    }
+}
+
+// Block sizes per graph: each block counts a contiguous chunk of vertices in
+// shared memory when the chunk lies in one graph.
+__global__ void k_block_sizes(const int32_t *truth, int64_t n, const int64_t *seg_off, int nseg, unsigned int *bsz,
+                              unsigned long long *ctr) {
+    __shared__ unsigned int s_h[NBINS];
+    const int64_t c0 = (int64_t)blockIdx.x * BS_CHUNK;
+    const int64_t c1 = min(c0 + BS_CHUNK, n);
+    const int s0 = seg_off ? seg_of(seg_off, nseg, c0) : 0;
+    const bool one = !seg_off || seg_of(seg_off, nseg, c1 - 1) == s0;
+    if (threadIdx.x < NBINS) s_h[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int64_t x = c0 + threadIdx.x; x < c1; x += blockDim.x) {
+        const int b = truth[x];
+        if (b < 0 || b >= NBINS) { flag_status(ctr, ST_BADGRAPH); continue; }
+        if (one) atomicAdd(&s_h[b], 1u);
+        else atomicAdd(&bsz[(int64_t)seg_of(seg_off, nseg, x) * NBINS + b], 1u);
+    }
+    __syncthreads();
+    if (one && threadIdx.x < NBINS && s_h[threadIdx.x])
+        atomicAdd(&bsz[(int64_t)s0 * NBINS + threadIdx.x], s_h[threadIdx.x]);
+}
+
+// Pass 1 of a level: component sizes into cur (zeroed), S_a into
+// sums[2 s + 1]; zeroes prev (the other buffer) for the next level.  Chunks
+// of VCHUNK vertices per warp, as in the snapshot; lanes grouped by
+// key_group; each warp adds its pair increments with one atomic per segment
+// change.
+__global__ void __launch_bounds__(256) k_ari_sizes(const int32_t *labels, int64_t n, const int64_t *seg_off, int nseg,
+                                                   unsigned int *cur, unsigned int *prev, unsigned long long *sums,
+                                                   unsigned long long *ctr) {
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const unsigned lane = lane_id();
+    int pend_s = -1;
+    unsigned long long pend = 0;
+    for (int64_t c0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * VCHUNK; c0 < n;
+         c0 += nw * VCHUNK) {
+        int32_t lab[VCHUNK_V];
+#pragma unroll
+        for (int v = 0; v < VCHUNK_V; ++v) {
+            const int64_t x = c0 + v * 32 + lane;
+            lab[v] = x < n ? labels[x] : 0;
+            if (x < n) prev[x] = 0u;
+        }
+        const int64_t cend = c0 + VCHUNK < n ? c0 + VCHUNK : n;
+        int sg = seg_off ? warp_seg_of(seg_off, nseg, c0, c0) : 0;
+        const bool uniform = !seg_off || sg + 1 >= nseg || seg_off[sg + 1] >= cend;
+        unsigned long long d = 0;
+#pragma unroll
+        for (int v = 0; v < VCHUNK_V; ++v) {
+            const int64_t x0 = c0 + v * 32, x = x0 + lane;
+            bool valid = x < n;
+            int s = sg;
+            if (!uniform) s = warp_seg_of(seg_off, nseg, x0 < n ? x0 : n - 1, valid ? x : n - 1);
+            int32_t root = -1;
+            if (valid) {
+                const int64_t r = (seg_off ? seg_off[s] : 0) + lab[v];
+                if (r < 0 || r >= n) {
+                    flag_status(ctr, ST_BADGRAPH);
+                    valid = false;
+                } else {
+                    root = (int32_t)r;
+                }
+            }
+            const unsigned same = key_group(valid, root);
+            unsigned long long dv = 0;
+            if (valid && lane == (unsigned)(__ffs(same) - 1)) {
+                const unsigned long long c = (unsigned long long)__popc(same);
+                dv = (unsigned long long)atomicAdd(&cur[root], (unsigned int)c) * c + c2(c);
+            }
+            if (uniform) d += dv;
+            else add_pairs(sums, 1, s, valid, dv);
+        }
+        if (uniform) {
+            d = warp_sum64(d);
+            if (sg != pend_s) {
+                if (lane == 0 && pend) atomicAdd(&sums[2 * pend_s + 1], pend);
+                pend_s = sg;
+                pend = 0;
+            }
+            pend += d;
         }
     }
+    if (lane == 0 && pend) atomicAdd(&sums[2 * pend_s + 1], pend);
+}
+
+// Pass 2 of a level: (root, block) cells of components with two or more
+// vertices, and S_ab into sums[2 s].
+__global__ void __launch_bounds__(256) k_ari_cells(const int32_t *labels, const int32_t *truth, int64_t n,
+                                                   const int64_t *seg_off, int nseg, unsigned long long tag,
+                                                   const unsigned int *size, unsigned long long *keys,
+                                                   unsigned long long *cnt, int bits, unsigned long long *sums,
+                                                   unsigned long long *ctr) {
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const unsigned lane = lane_id();
+    int pend_s = -1;
+    unsigned long long pend = 0;
+    for (int64_t c0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * VCHUNK; c0 < n;
+         c0 += nw * VCHUNK) {
+        const int64_t cend = c0 + VCHUNK < n ? c0 + VCHUNK : n;
+        int sg = seg_off ? warp_seg_of(seg_off, nseg, c0, c0) : 0;
+        const bool uniform = !seg_off || sg + 1 >= nseg || seg_off[sg + 1] >= cend;
+        int64_t root[VCHUNK_V];
+        int blk[VCHUNK_V];
+#pragma unroll
+        for (int v = 0; v < VCHUNK_V; ++v) {
+            const int64_t x = c0 + v * 32 + lane;
+            root[v] = -1;
+            blk[v] = -1;
+            if (x < n) {
+                const int s = uniform ? sg : warp_seg_of(seg_off, nseg, c0, x);
+                root[v] = (seg_off ? seg_off[s] : 0) + labels[x];
+                blk[v] = truth[x];
+            }
+        }
+        unsigned int sz[VCHUNK_V];
+#pragma unroll
+        for (int v = 0; v < VCHUNK_V; ++v) sz[v] = (root[v] >= 0 && root[v] < n) ? size[root[v]] : 0u;
+        unsigned long long d = 0;
+#pragma unroll
+        for (int v = 0; v < VCHUNK_V; ++v) {
+            const int64_t x0 = c0 + v * 32, x = x0 + lane;
+            // invalid roots and blocks are reported by the other passes
+            const bool valid = x < n && sz[v] >= 2 && blk[v] >= 0 && blk[v] < NBINS;
+            const unsigned long long key =
+                valid ? ((unsigned long long)root[v] << 6) | (unsigned long long)blk[v] : ~0ull;
+            const unsigned same = key_group(valid, key);
+            unsigned long long dv = 0;
+            if (valid && lane == (unsigned)(__ffs(same) - 1)) {
+                const int64_t slot = cell_slot(keys, bits, tag, key);
+                if (slot < 0) {
+                    flag_status(ctr, ST_BADGRAPH);
+                } else {
+                    const unsigned long long c = (unsigned long long)__popc(same);
+                    dv = tagged_add(&cnt[slot], tag, c) * c + c2(c);
+                }
+            }
+            if (uniform) {
+                d += dv;
+            } else {
+                const int s = warp_seg_of(seg_off, nseg, x0 < n ? x0 : n - 1, x < n ? x : n - 1);
+                add_pairs(sums, 0, s, x < n, dv);
+            }
+        }
+        if (uniform) {
+            d = warp_sum64(d);
+            if (sg != pend_s) {
+                if (lane == 0 && pend) atomicAdd(&sums[2 * pend_s], pend);
+                pend_s = sg;
+                pend = 0;
+            }
+            pend += d;
+        }
+    }
+    if (lane == 0 && pend) atomicAdd(&sums[2 * pend_s], pend);
 }
 
 __device__ double i128_to_double(__int128 v) {
@@ -149,18 +345,21 @@ __device__ double i128_to_double(__int128 v) {
     return neg ? -d : d;
 }
 
+// ARI of `levels` consecutive levels: sums is levels x nseg x (S_ab, S_a),
+// out is levels x nseg.
 __global__ void k_ari_final(const unsigned long long *sums, const unsigned int *bsz, const int64_t *seg_off, int nseg,
-                            int64_t n_all, double *out) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nseg) return;
+                            int levels, int64_t n_all, double *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)levels * nseg) return;
+    const int s = (int)(i % nseg);
     const int64_t nv = seg_off ? seg_off[s + 1] - seg_off[s] : n_all;
     unsigned long long sb = 0;
     for (int b = 0; b < NBINS; ++b) sb += c2(bsz[(int64_t)s * NBINS + b]);
-    const unsigned long long sab = sums[3 * s], sa = sums[3 * s + 1];
+    const unsigned long long sab = sums[2 * i], sa = sums[2 * i + 1];
     const unsigned long long T = (unsigned long long)nv * (unsigned long long)(nv > 0 ? nv - 1 : 0) / 2;
     const __int128 num = 2 * (__int128)T * sab - 2 * (__int128)sa * sb;
     const __int128 den = (__int128)T * (sa + sb) - 2 * (__int128)sa * sb;
-    out[s] = (nv < 2 || den == 0) ? 1.0 : i128_to_double(num) / i128_to_double(den);
+    out[i] = (nv < 2 || den == 0) ? 1.0 : i128_to_double(num) / i128_to_double(den);
 }
 
 // Per graph: the first level of highest ARI (ari is k x nseg).
@@ -212,27 +411,44 @@ int ari_table_bits(int64_t n) {
 }
 
 cudaError_t launch_ari(const int32_t *labels, int k, const int32_t *truth, int64_t n, const int64_t *seg_off, int nseg,
-                       unsigned int *bsz, unsigned int *size, unsigned long long *keys, unsigned int *cnt,
-                       unsigned long long *sums, double *out, unsigned long long *ctr, cudaStream_t s) {
+                       unsigned int *bsz, unsigned int *size, int64_t size_len, unsigned long long *keys,
+                       unsigned long long *cnt, int64_t tsize, unsigned long long *sums, double *out,
+                       unsigned long long *tag, unsigned long long *ctr, cudaStream_t s) {
     const int ns = seg_off ? nseg : 1;
     const int bits = ari_table_bits(n);
-    const int64_t tsize = (int64_t)1 << bits;
     cudaError_t e = cudaMemsetAsync(bsz, 0, (size_t)ns * NBINS * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    if (n > 0) k_block_sizes<<<grid_for(n), 256, 0, s>>>(truth, n, seg_off, ns, bsz, ctr);
-    int launched = n > 0 ? 1 : 0;
-    for (int L = 0; L < k; ++L) {
-        if ((e = cudaMemsetAsync(keys, 0xFF, (size_t)tsize * sizeof(unsigned long long), s)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(cnt, 0, (size_t)tsize * sizeof(unsigned int), s)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(size, 0, (size_t)(n > 0 ? n : 1) * sizeof(unsigned int), s)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(sums, 0, (size_t)3 * ns * sizeof(unsigned long long), s)) != cudaSuccess) return e;
-        if (n > 0) {
-            k_ari_cells<<<grid_for(n), 256, 0, s>>>(labels + (int64_t)L * n, truth, n, seg_off, ns, size, keys, cnt,
-                                                    bits, ctr);
-            k_ari_reduce<<<grid_for(tsize), 256, 0, s>>>(keys, cnt, tsize, size, n, seg_off, ns, sums);
+    int launched = 0;
+    if (n > 0) {
+        k_block_sizes<<<(unsigned)ceil_div(n, BS_CHUNK), 256, 0, s>>>(truth, n, seg_off, ns, bsz, ctr);
+        ++launched;
+    }
+    for (int L0 = 0; L0 < k; L0 += ARI_CHUNK) {
+        const int levels = k - L0 < ARI_CHUNK ? k - L0 : ARI_CHUNK;
+        if ((e = cudaMemsetAsync(sums, 0, (size_t)2 * ns * levels * sizeof(unsigned long long), s)) != cudaSuccess)
+            return e;
+        for (int L = L0; L < L0 + levels && n > 0; ++L) {
+            if (*tag >= TAG_LIMIT) {             // first use, or the tag would wrap: zero every word
+                if ((e = cudaMemsetAsync(size, 0, (size_t)2 * size_len * sizeof(unsigned int), s)) != cudaSuccess)
+                    return e;
+                if ((e = cudaMemsetAsync(keys, 0, (size_t)tsize * sizeof(unsigned long long), s)) != cudaSuccess)
+                    return e;
+                if ((e = cudaMemsetAsync(cnt, 0, (size_t)tsize * sizeof(unsigned long long), s)) != cudaSuccess)
+                    return e;
+                *tag = 0;
+            }
+            const unsigned long long t = ++*tag;
+            unsigned long long *ls = sums + (int64_t)2 * ns * (L - L0);
+            const int32_t *lab = labels + (int64_t)L * n;
+            unsigned int *cur = size + (t & 1ull) * size_len, *prev = size + ((t & 1ull) ^ 1ull) * size_len;
+            k_ari_sizes<<<vertex_pass_grid(n), 256, 0, s>>>(lab, n, seg_off, ns, cur, prev, ls, ctr);
+            k_ari_cells<<<vertex_pass_grid(n), 256, 0, s>>>(lab, truth, n, seg_off, ns, t, cur, keys, cnt, bits, ls,
+                                                            ctr);
             launched += 2;
         }
-        k_ari_final<<<(unsigned)ceil_div(ns, 128), 128, 0, s>>>(sums, bsz, seg_off, ns, n, out + (int64_t)L * ns);
+        const int64_t cells = (int64_t)levels * ns;
+        k_ari_final<<<(unsigned)ceil_div(cells, 128), 128, 0, s>>>(sums, bsz, seg_off, ns, levels, n,
+                                                                   out + (int64_t)L0 * ns);
         ++launched;
     }
     count_launches(launched);

@@ -10,13 +10,17 @@
 //    incident edge (64-bit atomicMax of the packed key at both roots) and the
 //    picked edges are hooked with the union-find; a pick that joins two trees
 //    is a forest edge (bit 7 of the level byte).  By the cut property, G_i and
-//    F_i = {e in F : L(e) >= i} have the same components for every i.
+//    F_i = {e in F : L(e) >= i} have the same components for every i.  The
+//    first round runs inside the level pass; later rounds read a list of the
+//    edges that still join two trees, compacted in place every round.
 // 2. Offline sweep: forest edges are bucketed by level; starting from
 //    singletons, level i = k .. 1 unions bucket i and then snapshots every
 //    vertex's root (the component minimum) as the labels at theta_i.
 // A batch of graphs is one disjoint union: with a segment table the snapshot
 // writes labels relative to each graph's first vertex and counts components
 // per graph.
+#include <atomic>
+
 #include "tec_internal.cuh"
 #include "uf.cuh"
 
@@ -25,20 +29,59 @@ namespace {
 
 constexpr uint8_t FOREST_BIT = 0x80;
 
-template <bool WIDE>
+__device__ __forceinline__ uint64_t msf_key(uint8_t L, int64_t j) {
+    return ((uint64_t)L << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)j);
+}
+
+// Exclusive prefix of per-thread counts over a TILE_THREADS block; *total gets the block sum.
+__device__ __forceinline__ int block_excl_prefix(int c, int *total) {
+    __shared__ int s_w[TILE_THREADS / 32];
+    const unsigned lane = lane_id();
+    const int w = (int)(threadIdx.x >> 5);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[w] = incl;
+    __syncthreads();
+    int base = 0, all = 0;
+#pragma unroll
+    for (int i = 0; i < TILE_THREADS / 32; ++i) {
+        base += i < w ? s_w[i] : 0;
+        all += s_w[i];
+    }
+    *total = all;
+    return base + incl - c;
+}
+
+// Edge levels and the first Boruvka round in one pass.  Every vertex is
+// still its own tree, so each edge with L >= 1 offers itself to both
+// endpoints.  With COMPACT the tile's offered edges are also written to its
+// region of the live-edge list (lu, lv, lk at [tile * TILE, + rcnt[tile])).
+template <bool WIDE, bool COMPACT>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_levels(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t, int64_t n, int64_t m,
-         int measure, const int64_t *tp, const int64_t *tq, int k, uint8_t *lvl, unsigned long long *ctr) {
-    if (graph_bad(ctr)) return;
+         int measure, const int64_t *tp, const int64_t *tq, int k, uint8_t *lvl, unsigned long long *best,
+         int32_t *lu, int32_t *lv, unsigned long long *lk, int32_t *rcnt, unsigned long long *ctr) {
+    if (graph_bad(ctr)) return;                  // uniform over the grid
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
     const int64_t klast = min(k0 + TILE, m) - 1;
     const int64_t r0 = row_search(ooff, 0, n - 1, k0);
     const int64_t r1 = row_search(ooff, r0, n - 1, klast);
+    int32_t eu[TILE_ITEMS], ev[TILE_ITEMS];
+    uint8_t el[TILE_ITEMS];
+    int c = 0;
+#pragma unroll
     for (int i = 0; i < TILE_ITEMS; ++i) {
         const int64_t j = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
-        if (j >= m) break;
+        el[i] = 0;
+        eu[i] = ev[i] = 0;
+        if (j >= m) continue;
         const int64_t u = row_search(ooff, r0, r1, j);
-        const int64_t s = (int64_t)deg[u] + deg[ocol[j]];
+        const int32_t v = ocol[j];
+        const int64_t s = (int64_t)deg[u] + deg[v];
         const uint32_t tt = t[j];
         int lo = 0, hi = k;                      // first threshold the edge does not survive
         while (lo < hi) {
@@ -46,11 +89,75 @@ k_levels(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uin
             if (keep_edge<WIDE>(measure, tt, s, tp[mid], tq[mid])) lo = mid + 1; else hi = mid;
         }
         lvl[j] = (uint8_t)lo;
+        el[i] = (uint8_t)lo;
+        eu[i] = (int32_t)u;
+        ev[i] = v;
+        if (lo) {
+            const unsigned long long key = msf_key((uint8_t)lo, j);
+            atomicMax(&best[u], key);
+            atomicMax(&best[v], key);
+            ++c;
+        }
     }
+    if (!COMPACT) return;
+    int total;
+    int at = block_excl_prefix(c, &total);
+#pragma unroll
+    for (int i = 0; i < TILE_ITEMS; ++i) {
+        if (!el[i]) continue;
+        const int64_t j = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
+        lu[k0 + at] = eu[i];
+        lv[k0 + at] = ev[i];
+        lk[k0 + at] = msf_key(el[i], j);
+        ++at;
+    }
+    if (threadIdx.x == 0) rcnt[blockIdx.x] = total;
 }
 
-__device__ __forceinline__ uint64_t msf_key(uint8_t L, int64_t j) {
-    return ((uint64_t)L << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)j);
+// A later Boruvka round over the live-edge list: each entry (tree roots of
+// both ends as of an earlier round, and the edge key) whose ends are still in
+// different trees offers itself to both current roots and stays in its
+// tile's region, stored by those roots; the others leave the list (trees
+// only merge, so such an edge never joins two trees again).  Every entry of
+// the region is read before the block's barrier and written after it.
+__global__ void __launch_bounds__(TILE_THREADS)
+k_msf_offer_list(int32_t *lu, int32_t *lv, unsigned long long *lk, int32_t *rcnt, int32_t *parent,
+                 unsigned long long *best) {
+    const int64_t base = (int64_t)blockIdx.x * TILE;
+    const int cnt = rcnt[blockIdx.x];
+    if (cnt == 0) return;                        // uniform over the block
+    int32_t ru[TILE_ITEMS], rv[TILE_ITEMS];
+    unsigned long long key[TILE_ITEMS];
+    unsigned live = 0;
+    int c = 0;
+#pragma unroll
+    for (int i = 0; i < TILE_ITEMS; ++i) {
+        const int idx = i * TILE_THREADS + (int)threadIdx.x;
+        ru[i] = rv[i] = 0;
+        key[i] = 0;
+        if (idx >= cnt) continue;
+        const int32_t a = uf_find(parent, lu[base + idx]);
+        const int32_t b = uf_find(parent, lv[base + idx]);
+        if (a == b) continue;
+        key[i] = lk[base + idx];
+        ru[i] = a;
+        rv[i] = b;
+        atomicMax(&best[a], key[i]);
+        atomicMax(&best[b], key[i]);
+        live |= 1u << i;
+        ++c;
+    }
+    int total;
+    int at = block_excl_prefix(c, &total);
+#pragma unroll
+    for (int i = 0; i < TILE_ITEMS; ++i) {
+        if (!((live >> i) & 1u)) continue;
+        lu[base + at] = ru[i];
+        lv[base + at] = rv[i];
+        lk[base + at] = key[i];
+        ++at;
+    }
+    if (threadIdx.x == 0) rcnt[blockIdx.x] = total;
 }
 
 // Every edge with L >= 1 between two different trees offers itself to both roots.
@@ -92,9 +199,17 @@ __global__ void k_msf_hook(const int64_t *ooff, const int32_t *ocol, uint8_t *lv
     }
 }
 
-__global__ void k_forest_count(const uint8_t *lvl, int64_t m, unsigned long long *bucket) {
+// Per-level forest-edge counts: a block histogram in shared memory, merged
+// into bucket[0 .. k] with one atomic per non-empty level per block.
+__global__ void k_forest_count(const uint8_t *lvl, int64_t m, int k, unsigned long long *bucket) {
+    __shared__ unsigned int hist[128];
+    for (int b = threadIdx.x; b <= k; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
-        if (lvl[j] & FOREST_BIT) atomicAdd(&bucket[lvl[j] & (uint8_t)~FOREST_BIT], 1ull);
+        if (lvl[j] & FOREST_BIT) atomicAdd(&hist[lvl[j] & (uint8_t)~FOREST_BIT], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b <= k; b += blockDim.x)
+        if (hist[b]) atomicAdd(&bucket[b], (unsigned long long)hist[b]);
 }
 
 // bucket[0 .. k] are the counts per level; this writes their exclusive scan
@@ -110,10 +225,28 @@ __global__ void k_forest_offsets(unsigned long long *bucket, int k) {
     bucket[2 * k + 2] = acc;
 }
 
+// Writes the forest edges of one tile to their level buckets: the tile's
+// per-level counts are reserved with one global atomic per level, then each
+// edge takes a slot from a shared-memory cursor.
 __global__ void __launch_bounds__(TILE_THREADS)
 k_forest_scatter(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_t n, int64_t m, int k,
                  unsigned long long *bucket, int32_t *fu, int32_t *fv) {
+    __shared__ unsigned int cnt[128];
+    __shared__ unsigned long long base[128];
+    for (int b = threadIdx.x; b <= k; b += blockDim.x) cnt[b] = 0;
+    __syncthreads();
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
+    for (int i = 0; i < TILE_ITEMS; ++i) {
+        const int64_t j = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
+        if (j >= m) break;
+        if (lvl[j] & FOREST_BIT) atomicAdd(&cnt[lvl[j] & (uint8_t)~FOREST_BIT], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b <= k; b += blockDim.x) {
+        base[b] = cnt[b] ? atomicAdd(&bucket[2 * k + 3 + b], (unsigned long long)cnt[b]) : 0ull;
+        cnt[b] = 0;
+    }
+    __syncthreads();
     const int64_t klast = min(k0 + TILE, m) - 1;
     const int64_t r0 = row_search(ooff, 0, n - 1, k0);
     const int64_t r1 = row_search(ooff, r0, n - 1, klast);
@@ -122,44 +255,84 @@ k_forest_scatter(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, i
         if (j >= m) break;
         if (!(lvl[j] & FOREST_BIT)) continue;
         const int L = lvl[j] & (uint8_t)~FOREST_BIT;
-        const unsigned long long at = atomicAdd(&bucket[2 * k + 3 + L], 1ull);
+        const unsigned long long at = base[L] + atomicAdd(&cnt[L], 1u);
+        if (at >= (unsigned long long)n) continue;   // a forest has < n edges; the host checks the total
         fu[at] = (int32_t)row_search(ooff, r0, r1, j);
         fv[at] = ocol[j];
     }
 }
 
-__global__ void k_union_bucket(const int32_t *fu, const int32_t *fv, const unsigned long long *bucket, int k, int L,
-                               int32_t *parent, unsigned long long *ctr) {
-    const int64_t b0 = (int64_t)bucket[k + 1 + L], b1 = (int64_t)bucket[k + 1 + L + 1];
+__global__ void k_union_bucket(const int32_t *fu, const int32_t *fv, int64_t b0, int64_t b1, int32_t *parent,
+                               unsigned long long *ctr) {
     for (int64_t e = b0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < b1; e += (int64_t)gridDim.x * blockDim.x)
         uf_link(parent, fu[e], fv[e], ctr);
 }
 
 // labels[x] = root of x (minus the first vertex of x's segment when a segment
-// table is given); ncomp[s] counts the roots of segment s.
-__global__ void k_snapshot(int32_t *parent, int64_t n, int32_t *labels, const int64_t *seg_off, int nseg,
-                           unsigned long long *ncomp) {
-    int roots = 0;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t r = uf_find(parent, (int32_t)x);
-        int64_t base = 0;
-        if (seg_off) {
-            int lo = 0, hi = nseg - 1;           // last segment starting at or before x
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (seg_off[mid] <= x) lo = mid; else hi = mid - 1;
-            }
-            base = seg_off[lo];
-            if (r == x) atomicAdd(&ncomp[lo], 1ull);
-        } else {
-            roots += (r == x) ? 1 : 0;
+// table is given); ncomp[s] counts the roots of segment s.  Each warp takes
+// chunks of VCHUNK consecutive vertices: the first parent loads of the whole
+// chunk are issued together, the segment is looked up once, and root counts
+// are summed per warp and added with one atomic whenever the segment changes
+// (per vertex only in the rare chunk that straddles a segment boundary).
+__global__ void __launch_bounds__(256) k_snapshot(int32_t *parent, int64_t n, int32_t *labels,
+                                                  const int64_t *seg_off, int nseg, unsigned long long *ncomp) {
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const unsigned lane = lane_id();
+    int pend_s = -1;
+    unsigned long long pend = 0;                 // roots counted for segment pend_s (lane 0)
+    for (int64_t c0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * VCHUNK; c0 < n;
+         c0 += nw * VCHUNK) {
+        int32_t r[VCHUNK_V];
+#pragma unroll
+        for (int v = 0; v < VCHUNK_V; ++v) {
+            const int64_t x = c0 + v * 32 + lane;
+            r[v] = x < n ? __ldcg(&parent[x]) : -1;
         }
-        labels[x] = (int32_t)(r - base);
+#pragma unroll
+        for (int v = 0; v < VCHUNK_V; ++v) {
+            const int64_t x = c0 + v * 32 + lane;
+            if (x < n) r[v] = uf_find_from(parent, (int32_t)x, r[v]);
+        }
+        const int64_t cend = c0 + VCHUNK < n ? c0 + VCHUNK : n;
+        int sg = 0;
+        bool uniform = true;
+        if (seg_off) {
+            sg = warp_seg_of(seg_off, nseg, c0, c0);
+            uniform = sg + 1 >= nseg || seg_off[sg + 1] >= cend;
+        }
+        if (uniform) {
+            const int64_t base = seg_off ? seg_off[sg] : 0;
+            int cnt = 0;
+#pragma unroll
+            for (int v = 0; v < VCHUNK_V; ++v) {
+                const int64_t x = c0 + v * 32 + lane;
+                if (x < n) {
+                    labels[x] = (int32_t)(r[v] - base);
+                    cnt += r[v] == x ? 1 : 0;
+                }
+            }
+            cnt = warp_sum(cnt);
+            if (sg != pend_s) {
+                if (lane == 0 && pend) atomicAdd(&ncomp[pend_s], pend);
+                pend_s = sg;
+                pend = 0;
+            }
+            pend += (unsigned long long)cnt;
+        } else {
+#pragma unroll
+            for (int v = 0; v < VCHUNK_V; ++v) {
+                const int64_t x0 = c0 + v * 32, x = x0 + lane;
+                const bool valid = x < n;
+                const int s = warp_seg_of(seg_off, nseg, x0 < n ? x0 : n - 1, valid ? x : n - 1);
+                if (valid) labels[x] = (int32_t)(r[v] - seg_off[s]);
+                const unsigned same = __match_any_sync(0xffffffffu, valid ? s : -1);
+                const unsigned rm = __ballot_sync(0xffffffffu, valid && r[v] == x) & same;
+                if (valid && rm && lane == (unsigned)(__ffs(same) - 1))
+                    atomicAdd(&ncomp[s], (unsigned long long)__popc(rm));
+            }
+        }
     }
-    if (!seg_off) {
-        roots = warp_sum(roots);
-        if (lane_id() == 0 && roots) atomicAdd(&ncomp[0], (unsigned long long)roots);
-    }
+    if (lane == 0 && pend) atomicAdd(&ncomp[pend_s], pend);
 }
 
 inline unsigned grid_for(int64_t work) {
@@ -169,23 +342,55 @@ inline unsigned grid_for(int64_t work) {
 
 }  // namespace
 
+unsigned vertex_pass_grid(int64_t n) {
+    static std::atomic<int> sms[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    int c = dev >= 0 && dev < 64 ? sms[dev].load(std::memory_order_relaxed) : 0;
+    if (c <= 0) {
+        if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0) c = 1;
+        if (dev >= 0 && dev < 64) sms[dev].store(c, std::memory_order_relaxed);
+    }
+    const int64_t blocks = ceil_div(ceil_div(n > 0 ? n : 1, VCHUNK), 8);
+    const int64_t cap = (int64_t)c * 16;
+    return (unsigned)(blocks < cap ? blocks : cap);
+}
+
 cudaError_t launch_levels(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
                           int64_t n, int64_t m, int measure, const int64_t *tp, const int64_t *tq, int k, bool wide,
-                          uint8_t *lvl, unsigned long long *ctr, cudaStream_t s) {
+                          uint8_t *lvl, unsigned long long *best, int32_t *lu, int32_t *lv, unsigned long long *lk,
+                          int32_t *rcnt, unsigned long long *ctr, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)ceil_div(m, TILE);
-    if (wide) k_levels<true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, measure, tp, tq, k, lvl, ctr);
-    else k_levels<false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, measure, tp, tq, k, lvl, ctr);
+    const bool compact = lu != nullptr;
+#define TEC_LEVELS(W, C) \
+    k_levels<W, C><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, measure, tp, tq, k, lvl, best, lu, lv, lk, \
+                                                 rcnt, ctr)
+    if (wide) {
+        if (compact) TEC_LEVELS(true, true); else TEC_LEVELS(true, false);
+    } else {
+        if (compact) TEC_LEVELS(false, true); else TEC_LEVELS(false, false);
+    }
+#undef TEC_LEVELS
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_msf_round(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int64_t m,
-                             int32_t *parent, unsigned long long *best, unsigned long long *ctr, cudaStream_t s) {
+cudaError_t launch_msf_offer(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int64_t m,
+                             int32_t *parent, unsigned long long *best, int32_t *lu, int32_t *lv,
+                             unsigned long long *lk, int32_t *rcnt, unsigned long long *ctr, cudaStream_t s) {
     if (m <= 0 || n <= 0) return cudaSuccess;
-    k_msf_offer<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, lvl, n, m, parent, best, ctr);
+    if (lu) k_msf_offer_list<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(lu, lv, lk, rcnt, parent, best);
+    else k_msf_offer<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, lvl, n, m, parent, best, ctr);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_msf_hook(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int32_t *parent,
+                            unsigned long long *best, unsigned long long *ctr, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
     k_msf_hook<<<grid_for(n), 256, 0, s>>>(ooff, ocol, lvl, n, parent, best, ctr);
-    count_launches(2);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -193,7 +398,8 @@ cudaError_t launch_forest_buckets(const int64_t *ooff, const int32_t *ocol, cons
                                   int k, unsigned long long *bucket, int32_t *fu, int32_t *fv, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(bucket, 0, (size_t)(k + 1) * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    if (m > 0) k_forest_count<<<grid_for(m), 256, 0, s>>>(lvl, m, bucket);
+    const int64_t cblocks = ceil_div(m, 4096);
+    if (m > 0) k_forest_count<<<(unsigned)(cblocks < 152 * 16 ? cblocks : 152 * 16), 256, 0, s>>>(lvl, m, k, bucket);
     k_forest_offsets<<<1, 1, 0, s>>>(bucket, k);
     if (m > 0)
         k_forest_scatter<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, lvl, n, m, k, bucket, fu, fv);
@@ -204,17 +410,24 @@ cudaError_t launch_forest_buckets(const int64_t *ooff, const int32_t *ocol, cons
 cudaError_t launch_snapshot(int32_t *parent, int64_t n, int32_t *labels, const int64_t *seg_off, int nseg,
                             unsigned long long *ncomp, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_snapshot<<<grid_for(n), 256, 0, s>>>(parent, n, labels, seg_off, nseg, ncomp);
+    k_snapshot<<<vertex_pass_grid(n), 256, 0, s>>>(parent, n, labels, seg_off, nseg, ncomp);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_level(const int32_t *fu, const int32_t *fv, const unsigned long long *bucket, int k, int L,
-                               int64_t n, int32_t *parent, int32_t *labels, const int64_t *seg_off, int nseg,
+cudaError_t launch_sweep_level(const int32_t *fu, const int32_t *fv, int64_t b0, int64_t b1, int64_t n,
+                               int32_t *parent, int32_t *labels, const int64_t *seg_off, int nseg,
                                unsigned long long *ncomp, unsigned long long *ctr, cudaStream_t s) {
-    k_union_bucket<<<grid_for(n), 256, 0, s>>>(fu, fv, bucket, k, L, parent, ctr);
-    if (n > 0) k_snapshot<<<grid_for(n), 256, 0, s>>>(parent, n, labels, seg_off, nseg, ncomp);
-    count_launches(n > 0 ? 2 : 1);
+    int launched = 0;
+    if (b1 > b0) {
+        k_union_bucket<<<grid_for(b1 - b0), 256, 0, s>>>(fu, fv, b0, b1, parent, ctr);
+        ++launched;
+    }
+    if (n > 0) {
+        k_snapshot<<<vertex_pass_grid(n), 256, 0, s>>>(parent, n, labels, seg_off, nseg, ncomp);
+        ++launched;
+    }
+    count_launches(launched);
     return cudaGetLastError();
 }
 

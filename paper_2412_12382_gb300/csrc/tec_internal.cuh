@@ -128,15 +128,25 @@ cudaError_t launch_upper_counts(const int64_t *off, const int32_t *col, int64_t 
 // sweep.cu: levels (number of sorted thresholds each edge survives), Boruvka
 // rounds of the maximum spanning forest (forest edges get bit 7 of lvl), the
 // level buckets of the forest edges, and one union + snapshot step per level.
+// Levels of every edge plus the first Boruvka round (offers into best, which
+// must be zero); with lu != nullptr also the live-edge list for later rounds
+// (lu, lv, lk with ceil(m / TILE) * TILE entries, rcnt one count per tile).
 cudaError_t launch_levels(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
                           int64_t n, int64_t m, int measure, const int64_t *tp, const int64_t *tq, int k, bool wide,
-                          uint8_t *lvl, unsigned long long *ctr, cudaStream_t s);
-cudaError_t launch_msf_round(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int64_t m,
-                             int32_t *parent, unsigned long long *best, unsigned long long *ctr, cudaStream_t s);
+                          uint8_t *lvl, unsigned long long *best, int32_t *lu, int32_t *lv, unsigned long long *lk,
+                          int32_t *rcnt, unsigned long long *ctr, cudaStream_t s);
+// A later Boruvka round's offers: from the live-edge list if lu != nullptr, else from the CSR.
+cudaError_t launch_msf_offer(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int64_t m,
+                             int32_t *parent, unsigned long long *best, int32_t *lu, int32_t *lv,
+                             unsigned long long *lk, int32_t *rcnt, unsigned long long *ctr, cudaStream_t s);
+// Hooks every root along its heaviest offer and clears the offers.
+cudaError_t launch_msf_hook(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int32_t *parent,
+                            unsigned long long *best, unsigned long long *ctr, cudaStream_t s);
 cudaError_t launch_forest_buckets(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_t n, int64_t m,
                                   int k, unsigned long long *bucket, int32_t *fu, int32_t *fv, cudaStream_t s);
-cudaError_t launch_sweep_level(const int32_t *fu, const int32_t *fv, const unsigned long long *bucket, int k, int L,
-                               int64_t n, int32_t *parent, int32_t *labels, const int64_t *seg_off, int nseg,
+// Unions the forest edges fu/fv[b0, b1) (one level's bucket), then snapshots the labels.
+cudaError_t launch_sweep_level(const int32_t *fu, const int32_t *fv, int64_t b0, int64_t b1, int64_t n,
+                               int32_t *parent, int32_t *labels, const int64_t *seg_off, int nseg,
                                unsigned long long *ncomp, unsigned long long *ctr, cudaStream_t s);
 
 cudaError_t launch_snapshot(int32_t *parent, int64_t n, int32_t *labels, const int64_t *seg_off, int nseg,
@@ -148,9 +158,16 @@ cudaError_t launch_features(const int64_t *ooff, const int32_t *ocol, const int3
                             unsigned long long *ctr, cudaStream_t s);
 int ari_table_bits(int64_t n);
 cudaError_t launch_best_level(const double *ari, int k, int nseg, int32_t *best, double *best_ari, cudaStream_t s);
+// ARI_CHUNK levels share one zeroing of the pair sums (sums holds 2 x nseg x ARI_CHUNK).
+constexpr int ARI_CHUNK = 64;
+// size holds two arrays of size_len >= n counters used in turn (by the
+// parity of the level tag); keys / cnt (tsize = 2^ari_table_bits(n_cap)
+// slots) are level-tagged.  *tag advances by one per level; a *tag of
+// ~0 (or one about to wrap) zeroes all three first.
 cudaError_t launch_ari(const int32_t *labels, int k, const int32_t *truth, int64_t n, const int64_t *seg_off, int nseg,
-                       unsigned int *bsz, unsigned int *size, unsigned long long *keys, unsigned int *cnt,
-                       unsigned long long *sums, double *out, unsigned long long *ctr, cudaStream_t s);
+                       unsigned int *bsz, unsigned int *size, int64_t size_len, unsigned long long *keys,
+                       unsigned long long *cnt, int64_t tsize, unsigned long long *sums, double *out,
+                       unsigned long long *tag, unsigned long long *ctr, cudaStream_t s);
 
 // cc.cu
 cudaError_t launch_cc_init(int32_t *parent, int64_t n, cudaStream_t s);
@@ -169,6 +186,29 @@ __device__ __forceinline__ int warp_sum(int x) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
 }
+
+// Segment of vertex x (the last s with seg_off[s] <= x) for lanes that hold
+// x = x0 + lane with x0 warp-uniform: every lane runs the same binary search
+// for x0 (broadcast loads), then walks forward over at most 31 segment starts.
+__device__ __forceinline__ int warp_seg_of(const int64_t *seg_off, int nseg, int64_t x0, int64_t x) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg_off[mid] <= x0) lo = mid; else hi = mid - 1;
+    }
+    while (lo + 1 < nseg && seg_off[lo + 1] <= x) ++lo;
+    return lo;
+}
+
+// Vertex passes (snapshot, ARI) hand each warp chunks of VCHUNK_V x 32
+// consecutive vertices: one segment lookup per chunk, VCHUNK_V independent
+// loads in flight per lane.
+constexpr int VCHUNK_V = 8;
+constexpr int VCHUNK = 32 * VCHUNK_V;
+
+// Grid for a persistent vertex pass of 256-thread blocks: enough warps for
+// every chunk, at most 16 blocks per SM.
+unsigned vertex_pass_grid(int64_t n);
 
 // Largest r in [lo, hi] with off[r] <= k (off non-decreasing, off[lo] <= k).
 __device__ __forceinline__ int64_t row_search(const int64_t *off, int64_t lo, int64_t hi, int64_t k) {
@@ -247,6 +287,10 @@ struct tec_graph {
     // sweep scratch, allocated on first sweep
     uint8_t *lvl = nullptr;         // m: level of each oriented edge, bit 7 = forest edge
     unsigned long long *best = nullptr;   // n: Boruvka offers
+    int32_t *msf_u = nullptr, *msf_v = nullptr;  // live-edge list: tree roots of both ends
+    unsigned long long *msf_k = nullptr;  // live-edge list: edge keys
+    int32_t *msf_cnt = nullptr;           // live entries per tile region
+    int64_t msf_cap = 0;                  // entries allocated (0: no list, rounds rescan the CSR)
     int32_t *fu = nullptr, *fv = nullptr; // n: forest edges bucketed by level
     unsigned long long *bucket = nullptr; // 3k+4 bucket counts / offsets / cursors
     int64_t *thr = nullptr;         // 2 * 128 sorted thresholds (p then q)
@@ -255,10 +299,12 @@ struct tec_graph {
     // features / ARI scratch, grown on demand
     unsigned int *seg_hist = nullptr;      // nseg x 64 (histogram, block sizes)
     int64_t seg_cap = 0;
-    unsigned long long *ari_sums = nullptr; // 3 x nseg
-    unsigned int *ari_size = nullptr;      // n_cap
-    unsigned long long *ari_keys = nullptr; // 2^bits cell keys
-    unsigned int *ari_cnt = nullptr;       // 2^bits cell counts
+    unsigned long long *ari_sums = nullptr; // 2 x nseg x ARI_CHUNK pair sums
+    unsigned int *ari_size = nullptr;      // 2 x n_cap component sizes (two levels in turn)
+    int64_t ari_n = -1;                     // vertex count the ARI counters were last used with
+    unsigned long long *ari_keys = nullptr; // 2^bits level-tagged cell keys
+    unsigned long long *ari_cnt = nullptr;  // 2^bits level-tagged cell counts
+    unsigned long long ari_tag = 0;         // last level tag used in the arrays above
     unsigned long long *ctr = nullptr;      // device counter block
     unsigned long long *ctr_host = nullptr; // pinned mirror for reads
 

@@ -11,8 +11,8 @@
 
 namespace tec {
 
-__device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x) {
-    int32_t cur = __ldcg(&parent[x]);
+// Root of x given cur = parent[x] already loaded (lets callers batch the first loads).
+__device__ __forceinline__ int32_t uf_find_from(int32_t *parent, int32_t x, int32_t cur) {
     if (cur != x) {
         int32_t prev = x, next;
         while (cur > (next = __ldcg(&parent[cur]))) {
@@ -22,6 +22,10 @@ __device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x) {
         }
     }
     return cur;
+}
+
+__device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x) {
+    return uf_find_from(parent, x, __ldcg(&parent[x]));
 }
 
 // Each failed compare-and-swap means a root was hooked by another thread, so

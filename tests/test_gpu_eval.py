@@ -93,3 +93,32 @@ def test_ari_random_labelings(tec):
     same = g.ari(torch.from_numpy(truth[None, :].copy()).cuda(), torch.from_numpy(truth).cuda()).cpu().numpy()
     assert same[0, 0] == 1.0
     g.free()
+
+
+def test_ari_many_levels_tiny_segments_repeated(tec):
+    """150 labelings (three chunks of levels) of a batch whose graphs have 1,
+    2, 31, 33, 64 and 200 vertices, so warps straddle graph boundaries;
+    called twice so the second call reuses counters tagged by the first."""
+    import torch
+    rng = np.random.default_rng(11)
+    sizes = [1, 2, 31, 1, 33, 64, 2, 200, 5]
+    graphs = [small.gnp(s, 0.1, rng) if s > 1 else small.empty(1) for s in sizes]
+    off, col, seg = disjoint_union(graphs)
+    n = int(seg[-1])
+    g = _graph(tec, off, col)
+    segd = torch.from_numpy(seg).cuda()
+    k = 150
+    labs = np.empty((k, n), dtype=np.int32)
+    for L in range(k):
+        for i, s in enumerate(sizes):
+            ncl = 1 + L % max(1, s)
+            labs[L, seg[i]:seg[i + 1]] = rng.integers(0, min(ncl, s), s)
+    truth = np.concatenate([rng.integers(0, 64 if L % 2 else 3, s) for L, s in enumerate(sizes)]).astype(np.int32)
+    labd, truthd = torch.from_numpy(labs).cuda(), torch.from_numpy(truth).cuda()
+    for _ in range(2):
+        ari = g.ari(labd, truthd, segd).cpu().numpy()
+        for L in range(k):
+            for i in range(len(sizes)):
+                ref = O.ari(labs[L, seg[i]:seg[i + 1]], truth[seg[i]:seg[i + 1]])
+                assert abs(ari[L, i] - ref) <= 2e-15, (L, i, ari[L, i], ref)
+    g.free()

@@ -271,7 +271,7 @@ tec_status tec_graph_create(int64_t n_cap, int64_t nnz_cap, void *stream, tec_gr
     if (s == TEC_OK) s = dalloc(&g->col, nnz_cap, "column ids");
     if (s == TEC_OK) s = dalloc(&g->deg, n_cap, "degrees");
     if (s == TEC_OK) s = dalloc(&g->ooff, n_cap + 1, "oriented offsets");
-    if (s == TEC_OK) s = dalloc(&g->ocol, g->m_cap, "oriented column ids");
+    if (s == TEC_OK) s = dalloc(&g->ocol, g->m_cap + 4, "oriented column ids");   // 16-byte padded for bulk prefetches
     if (s == TEC_OK) s = dalloc(&g->t, g->m_cap, "triangle counts");
     if (s == TEC_OK) s = dalloc(&g->keep, mwords, "keep mask");
     if (s == TEC_OK) s = dalloc(&g->parent, n_cap, "union-find parents");

@@ -41,7 +41,11 @@ constexpr int W_MAX = 256;                      // largest d+(c) of a warp visit
 constexpr int B_THREADS = 512;                  // block-visit kernel block
 constexpr int B_WARPS = B_THREADS / 32;
 constexpr int S_CHUNK = 4096;                   // staged ids per block chunk
-constexpr int64_t VISIT_PROBES = 1 << 20;       // target probes per visit
+constexpr int64_t VISIT_PROBES_W = 1 << 20;     // target probes per warp visit
+// Target probes per block visit.  A block visit ends at a block barrier, so
+// its warps idle for up to one 32-candidate batch at the end: the visit must
+// hold many batches per warp for that tail to stay small.
+constexpr int64_t VISIT_PROBES_B = 1 << 25;
 constexpr int W_GRAB = 16;                      // warp visits taken per counter bump
 constexpr uint64_t VIS_MASK = (1ull << 32) - 1;
 
@@ -59,7 +63,7 @@ __device__ __forceinline__ int64_t lower_bound_g(const int32_t *a, int64_t lo, i
 
 // Candidates of one visit: du + deg candidates split into slices of vlen.
 __device__ __forceinline__ int64_t visit_len(int64_t du) {
-    int64_t v = VISIT_PROBES / (du > 0 ? du : 1);
+    int64_t v = (du <= W_MAX ? VISIT_PROBES_W : VISIT_PROBES_B) / (du > 0 ? du : 1);
     return v < 256 ? 256 : (v > 65536 ? 65536 : v);
 }
 
@@ -152,6 +156,7 @@ __device__ __forceinline__ Cand load_cand(const int64_t *off, const int32_t *col
 // scan.
 
 constexpr int QCAP = 64;                 // per-warp queue of filter positives
+constexpr int PF_DEPTH = 2;              // long probe rows pulled into L2 ahead of the warp's loads
 constexpr int UNROLL = 4;                // ids loaded per lane before the first is probed
 constexpr int SHORT_ROW = 96;            // rows up to this length are packed across lanes
 
@@ -175,6 +180,15 @@ struct Staged {
     int32_t base;
     int nb;
 };
+
+// Bulk prefetch of ids [start, start + count) of a (16-byte aligned, padded to
+// a multiple of 16 bytes) id array into L2: one instruction per row, issued
+// by one lane; the range is widened to 16-byte boundaries.
+__device__ __forceinline__ void l2_prefetch_ids(const int32_t *a, int64_t start, int64_t count) {
+    const int64_t a0 = start & ~(int64_t)3, a1 = (start + count + 3) & ~(int64_t)3;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a + a0), "r"((uint32_t)((a1 - a0) * 4))
+                 : "memory");
+}
 
 __device__ __forceinline__ uint32_t fhash(int32_t w, int fb) {
     return ((uint32_t)w * 0x9E3779B1u) >> (32 - fb);
@@ -287,11 +301,22 @@ __device__ __forceinline__ void process_batch(const int64_t *off, const int32_t 
     ws.jpos[lane] = cd.jpos;
     __syncwarp();
     int qn = 0;
-    // long rows, one after another
+    // long rows, one after another; the first PF_DEPTH are pulled into L2 now
+    // and each row started pulls the one PF_DEPTH rows later
     unsigned todo = __ballot_sync(FULL, cd.len > SHORT_ROW);
+    unsigned pf = todo;
+    {
+        const unsigned rank = __popc(todo & ((1u << lane) - 1u));
+        if (((todo >> lane) & 1u) && rank < PF_DEPTH) l2_prefetch_ids(ocol, cd.rs, cd.len);
+        for (int i = 0; i < PF_DEPTH && pf; ++i) pf &= pf - 1;
+    }
     while (todo) {
         const int src = __ffs(todo) - 1;
         todo &= todo - 1;
+        if (pf) {
+            if ((int)lane == __ffs(pf) - 1) l2_prefetch_ids(ocol, cd.rs, cd.len);
+            pf &= pf - 1;
+        }
         const int64_t rs = __shfl_sync(FULL, cd.rs, src);
         const int len = __shfl_sync(FULL, cd.len, src);
         for (int base = 0; base < len; base += 32 * UNROLL) {

@@ -43,7 +43,7 @@ WORKLOADS = {
 # DRAM bytes per launch of the triangle-count stage from an ncu capture, per
 # unit of algorithmic bytes, valid only for the support.cu it was taken on
 # (see profiles/).  None until a capture exists for the current source.
-TRAFFIC_CAPTURE = {"support_sha": "539a64f0de07566b", "dram_per_alg_byte": 82.2969 / 49.162954,
+TRAFFIC_CAPTURE = {"support_sha": "f077fe23de50fc0b", "dram_per_alg_byte": 84.066287 / 49.162954,
                    "source": "ncu DRAM bytes of k_support at R-MAT scale 22, scaled by algorithmic bytes"}
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -243,10 +243,13 @@ def bench_batched_sweep(reps=3):
 
 
 def bench_picker(reps=3):
-    """Held-out DC-SBM graphs (seeds 20000-20499, n in [1000, 100000]) as one
-    batch.  Picker path: features, bf16 network, grid thresholds, one batched
-    prune + components.  Sweep path: 64-threshold sweep, 64 ARI evaluations,
-    best level.  The triangle counts, shared by both, are timed apart."""
+    """Held-out DC-SBM graphs (seeds 20000-20499, n log-uniform in [1000,
+    100000]) as one batch, with the shipped picker checkpoint.
+    Picker path: tec_pick_threshold (features, bf16 network, grid threshold)
+    and one batched prune + components.  Sweep path: components at the 64
+    thresholds b/128 (64 independent batched passes; the spanning-forest sweep
+    is reported beside it), 64 ARI evaluations and the best level per graph.
+    The triangle counts, shared by both, are timed apart."""
     import numpy as np
     import torch
     from graphgen.gpu import dcsbm_batch_gpu
@@ -258,30 +261,46 @@ def bench_picker(reps=3):
     off, col, seg, truth, specs = dcsbm_batch_gpu(list(range(20000, 20500)), 1000, 100000)
     g = Graph(off, col)
     stream = g.stream
+    nseg = seg.numel() - 1
     sup_ms, _ = _timed(lambda: g.support(), stream, 2)
+    lab_all = torch.empty((PK.K, g.n), dtype=torch.int32, device="cuda")
+    thr = [(torch.full((nseg,), b, dtype=torch.int64, device="cuda"),
+            torch.full((nseg,), PK.DEN, dtype=torch.int64, device="cuda")) for b in PK.GRID_P]
 
     def picker_path():
-        y = pk.forward(g.features(seg), bf16=True)
-        p, q = T.picker_thresholds(y)
+        p, q = g.pick_threshold(pk, seg, bf16=True)
         return g.prune_components_batch(TECTONIC, p, q, seg, count=False)[0]
 
-    def sweep_path():
+    def sweep_independent():
+        for L, (p, q) in enumerate(thr):
+            g.prune_components_batch(TECTONIC, p, q, seg, labels=lab_all[L], count=False)
+        return T.ari_best(g.ari(lab_all, truth, seg))
+
+    def sweep_msf():
         labels, _ = g.sweep(TECTONIC, PK.GRID_P, PK.GRID_Q, seg_off=seg, count=False)
-        ari = g.ari(labels, truth, seg)
-        return T.ari_best(ari)
+        return T.ari_best(g.ari(labels, truth, seg))
 
     picker_ms, plab = _timed(picker_path, stream, reps + 1)
-    sweep_ms, (best, best_ari) = _timed(sweep_path, stream, reps + 1)
+    ind_ms, (best_i, best_ari_i) = _timed(sweep_independent, stream, reps)
+    msf_ms, (best, best_ari) = _timed(sweep_msf, stream, reps + 1)
     got = g.ari(plab[None, :], truth, seg)[0]
+    ari_all = g.ari(lab_all, truth, seg)
+    fixed_level = int(meta.get("eval", {}).get("fixed_level", 8)) - 1
     d = (best_ari - got).cpu().numpy()
+    out = {"workload": "500 held-out DC-SBM graphs, seeds 20000-20499, n log-uniform in [1e3, 1e5]",
+           "graphs": int(nseg), "n": int(g.n), "m": int(g.m), "picker_ms": picker_ms,
+           "sweep_independent_ms": ind_ms, "sweep_msf_ms": msf_ms,
+           "ratio_sweep_over_picker": ind_ms / picker_ms, "ratio_msf_sweep_over_picker": msf_ms / picker_ms,
+           "support_ms": sup_ms, "ratio_including_support": (ind_ms + sup_ms) / (picker_ms + sup_ms),
+           "ratio_msf_including_support": (msf_ms + sup_ms) / (picker_ms + sup_ms),
+           "same_best_both_sweeps": bool(torch.equal(best, best_i)),
+           "mean_dARI": float(d.mean()), "p95_dARI": float(np.percentile(d, 95)), "max_dARI": float(d.max()),
+           "mean_ARI_picker": float(got.mean()), "mean_ARI_best": float(best_ari.mean()),
+           "mean_ARI_fixed": float(ari_all[fixed_level].mean()), "fixed_threshold": f"{fixed_level + 1}/128",
+           "inference": "bf16", "trained_on": meta.get("train_seeds"), "epochs_kept": meta.get("epochs_kept")}
     g.free()
     pk.free()
-    return {"workload": "500 held-out DC-SBM graphs, seeds 20000-20499, n log-uniform in [1e3, 1e5]",
-            "graphs": int(seg.numel() - 1), "picker_ms": picker_ms, "sweep_ms": sweep_ms,
-            "ratio_sweep_over_picker": sweep_ms / picker_ms, "support_ms": sup_ms,
-            "ratio_including_support": (sweep_ms + sup_ms) / (picker_ms + sup_ms),
-            "mean_dARI": float(d.mean()), "p95_dARI": float(np.percentile(d, 95)), "max_dARI": float(d.max()),
-            "inference": "bf16", "trained_on": meta.get("train_seeds"), "epochs_kept": meta.get("epochs_kept")}
+    return out
 
 
 def run_reference(args, spec, rank, world):
@@ -332,6 +351,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched sweep measurement")
     ap.add_argument("--no-picker", action="store_true", help="skip the picker-vs-sweep measurement")
+    ap.add_argument("--only", choices=["sweep", "picker"], default=None,
+                    help="profiling aid: run only the batched sweep or only the picker-vs-sweep block "
+                         "and print its result (not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warning: fewer than 3 warm-up steps")
@@ -363,6 +385,10 @@ def main():
     from paper_2412_12382_gb300 import build as libbuild
     from paper_2412_12382_gb300 import tectonic as T
     libbuild.build()
+    if args.only:
+        res = bench_batched_sweep() if args.only == "sweep" else bench_picker()
+        print(json.dumps({"only": args.only, "result": res}), flush=True)
+        return 0
 
     t0 = time.time()
     off, col = make_workload(spec, dev)

@@ -282,6 +282,17 @@ tec_status tec_picker_adam_step(tec_picker *p, const float *grad, float lr, floa
 tec_status tec_picker_train(tec_picker *p, const float *feats, const float *target, int64_t N, int epochs, int batch,
                             float lr, uint64_t seed, float *loss_out);
 
+/* The learned threshold of every graph of a batch (the whole graph if
+ * seg_off is NULL): tec_features, the picker network (bf16 != 0: bfloat16
+ * inference as in tec_picker_forward) and the grid threshold of
+ * tec_picker_thresholds, in one call on the graph's stream (ordered after
+ * work already queued on the picker's stream, and before the picker's next
+ * use).  p_out, q_out: device, nseg int64 each (one without segments), ready
+ * for tec_prune_components_batch.  Runs tec_support if needed.  The paper
+ * picks thresholds by rules of thumb (Sec. IV-E); this call replaces them. */
+tec_status tec_pick_threshold(tec_graph *g, tec_picker *p, const int64_t *seg_off, int nseg, int bf16,
+                              int64_t *p_out, int64_t *q_out);
+
 /* Grid thresholds from picker outputs y (device, N float32): b =
  * clamp(round(64 y), 1, 64) (non-finite y gives 1), p_out[i] = b,
  * q_out[i] = 128 (device int64 arrays), on `stream`. */

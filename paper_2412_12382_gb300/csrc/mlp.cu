@@ -342,6 +342,37 @@ tec_status tec_picker_forward(tec_picker *p, const float *feats, int64_t N, int 
     return TEC_OK;
 }
 
+// Orders stream `after` behind the work queued so far on stream `before`.
+static tec_status stream_after(cudaStream_t before, cudaStream_t after) {
+    if (before == after) return TEC_OK;
+    cudaEvent_t ev;
+    TEC_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, before);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(after, ev, 0);
+    cudaEventDestroy(ev);
+    TEC_CUDA(e);
+    return TEC_OK;
+}
+
+tec_status tec_pick_threshold(tec_graph *g, tec_picker *p, const int64_t *seg_off, int nseg, int bf16,
+                              int64_t *p_out, int64_t *q_out) {
+    clear_error();
+    if (!g || !p || !p_out || !q_out) return set_error(TEC_EINVAL, "NULL argument");
+    if (seg_off && nseg < 1) return set_error(TEC_EINVAL, "nseg must be >= 1 with a segment table");
+    const int64_t ns = seg_off ? nseg : 1;
+    TEC_TRY(picker_work(p, ns));
+    TEC_TRY(stream_after(p->stream, g->stream));    // parameters and work buffers settled
+    TEC_TRY(tec_features(g, seg_off, nseg, p->X));
+    clear_error();
+    if (bf16) k_forward<true><<<(unsigned)ns, HID, 0, g->stream>>>(p->P, p->X, ns, nullptr, nullptr, p->Y);
+    else k_forward<false><<<(unsigned)ns, HID, 0, g->stream>>>(p->P, p->X, ns, nullptr, nullptr, p->Y);
+    k_pick<<<(unsigned)ceil_div(ns, 256), 256, 0, g->stream>>>(p->Y, ns, p_out, q_out);
+    count_launches(2);
+    TEC_CUDA(cudaGetLastError());
+    TEC_TRY(stream_after(g->stream, p->stream));    // the picker's next use waits for its buffers
+    return TEC_OK;
+}
+
 tec_status tec_picker_loss_grad(tec_picker *p, const float *feats, const float *target, int64_t N, float *loss_out,
                                 float *grad_out) {
     clear_error();

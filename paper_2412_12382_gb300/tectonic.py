@@ -72,6 +72,7 @@ SIGNATURES = {
     "tec_picker_train": ([_P, _P, _P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64, _P],
                          ctypes.c_int),
     "tec_picker_thresholds": ([_P, _I64, _P, _P, _P], ctypes.c_int),
+    "tec_pick_threshold": ([_P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
     "tec_components_noalloc": ([_I64, _I64, _P, _P, _P, _P, _PI64, _P], ctypes.c_int),
 }
 
@@ -314,6 +315,16 @@ class Graph:
         check(self._lib.tec_ari(self._h, k, _ptr(labels.contiguous()), _ptr(truth.contiguous()),
                                 _ptr(seg_off) if seg_off is not None else None, nseg, _ptr(out)))
         return out
+
+    def pick_threshold(self, picker, seg_off=None, bf16: bool = True):
+        """Learned grid threshold per graph: (p, q) CUDA int64 tensors (nseg, or 1 without segments)."""
+        torch = _torch()
+        nseg = 0 if seg_off is None else seg_off.numel() - 1
+        p = torch.empty(max(nseg, 1), dtype=torch.int64, device="cuda")
+        q = torch.empty(max(nseg, 1), dtype=torch.int64, device="cuda")
+        check(self._lib.tec_pick_threshold(self._h, picker._h, _ptr(seg_off) if seg_off is not None else None, nseg,
+                                           int(bf16), _ptr(p), _ptr(q)))
+        return p, q
 
     def prune_components_batch(self, measure: int, p, q, seg_off, labels=None, count: bool = True):
         """Per-graph thresholds p[s]/q[s] (CUDA int64): local labels (n) and components per graph."""

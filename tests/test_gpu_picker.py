@@ -117,3 +117,33 @@ def test_picker_gains_over_one_fixed_threshold(tec):
     assert losses[-1] < losses[0]
     assert res["mean_dARI"] < res["fixed_mean_dARI"]
     pk.free()
+
+
+def test_pick_threshold_equals_features_forward_thresholds(tec):
+    """The one-call picker entry point gives exactly the grid thresholds of
+    features -> network -> thresholds, per graph of a batch, in float32 and
+    bfloat16 inference, and for a single graph without a segment table."""
+    import torch
+    from graphgen.dcsbm import dcsbm_csr
+    from graphgen.batch import disjoint_union
+    from paper_2412_12382_gb300 import tectonic as T
+    from paper_2412_12382_gb300.tectonic import Picker
+    graphs = [dcsbm_csr(s, 300, 3000)[:2] for s in range(30500, 30512)]
+    off, col, seg = disjoint_union(graphs)
+    g = tec.Graph(torch.from_numpy(off).cuda(), torch.from_numpy(col).cuda())
+    segd = torch.from_numpy(seg).cuda()
+    theta = M.init(7).astype(np.float32)
+    theta[-1] = 0.2
+    pk = Picker(theta)
+    for bf16 in (False, True):
+        p, q = g.pick_threshold(pk, segd, bf16=bf16)
+        pr, qr = T.picker_thresholds(pk.forward(g.features(segd), bf16=bf16))
+        assert torch.equal(p, pr) and torch.equal(q, qr)
+        assert int(p.min()) >= 1 and int(p.max()) <= 64 and bool((q == 128).all())
+    g.free()
+    g1 = tec.Graph(torch.from_numpy(np.asarray(graphs[0][0])).cuda(), torch.from_numpy(np.asarray(graphs[0][1])).cuda())
+    p1, q1 = g1.pick_threshold(pk)
+    pr1, qr1 = T.picker_thresholds(pk.forward(g1.features()))
+    assert p1.shape == (1,) and torch.equal(p1, pr1) and torch.equal(q1, qr1)
+    g1.free()
+    pk.free()

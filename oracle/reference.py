@@ -293,3 +293,74 @@ def features(off, eu, ev, t):
     if m == 0:
         return np.concatenate([h, [0.0, 0.0]])
     return np.concatenate([h / m, [math.log(2.0 * m / n), math.log(m)]])
+
+
+# ------------------------------------------------------ sweep diagnostics, rules of thumb
+
+
+def sweep_stats(off, col, measure: int, ps, qs, labels, nthreads: int = 1):
+    """Per threshold p_i/q_i, the statistics Sec. IV-E plots against the
+    threshold (Fig. 6), for the labeling labels[i] of that threshold:
+    ncomp (components), kept (edges with sim >= p_i/q_i), largest (size of the
+    largest component), intra (edges of the input graph inside one component)
+    and the modularity of Sec. II with the components as communities,
+    Q = intra/m - sum_c vol(c)^2 / (2m)^2, vol(c) the degree sum of c,
+    formed from exact integers and rounded once (0 for a graph without edges)."""
+    from fractions import Fraction
+    off, col = _csr(off, col)
+    n = len(off) - 1
+    eu, ev = edge_list(off, col)
+    t, uni = edge_counts(off, col, eu, ev, nthreads)
+    deg = degrees(off)
+    m = len(eu)
+    out = []
+    for i, (p, q) in enumerate(zip(ps, qs)):
+        _, kept = prune(measure, off, eu, ev, t, uni, p, q)
+        lab = np.asarray(labels[i], dtype=np.int64)
+        _, li = np.unique(lab, return_inverse=True)
+        size = np.bincount(li)
+        vol = np.zeros(len(size), dtype=np.int64)
+        np.add.at(vol, li, deg)
+        intra = int(np.count_nonzero(lab[eu] == lab[ev]))
+        sum_vol2 = sum(int(v) * int(v) for v in vol)
+        qmod = float(Fraction(4 * m * intra - sum_vol2, 4 * m * m)) if m else 0.0
+        out.append({"ncomp": int(len(size)), "kept": int(kept), "largest": int(size.max()) if n else 0,
+                    "intra": intra, "sum_vol2": sum_vol2, "modularity": qmod})
+    return out
+
+
+def _ascending(ps, qs):
+    from fractions import Fraction
+    return sorted(range(len(ps)), key=lambda i: (Fraction(int(ps[i]), int(qs[i])), i))
+
+
+def rule_largest_jump(ps, qs, largest):
+    """Rule of thumb R1 (Sec. IV-E): visit the thresholds in decreasing order
+    and stop at the sudden increase of the largest component: the index of the
+    threshold just above the largest increase (the highest such threshold on
+    ties), or None when the largest component never grows."""
+    order = _ascending(ps, qs)
+    best, best_jump = None, 0
+    for j in range(len(order) - 2, -1, -1):          # from theta_(j+1) down to theta_j
+        jump = largest[order[j]] - largest[order[j + 1]]
+        if jump > best_jump:
+            best, best_jump = order[j + 1], jump
+    return best
+
+
+def rule_modularity(ps, qs, modularity):
+    """Rule of thumb R2 (Sec. IV-E): the threshold of largest modularity (the
+    lowest such threshold on ties)."""
+    order = _ascending(ps, qs)
+    best = order[0]
+    for i in order[1:]:
+        if modularity[i] > modularity[best]:
+            best = i
+    return best
+
+
+def rule_of_thumb(ps, qs, stats):
+    """R1, falling back to R2 where the largest component never grows (the
+    paper recommends modularity where no shift shows)."""
+    r1 = rule_largest_jump(ps, qs, [s["largest"] for s in stats])
+    return r1 if r1 is not None else rule_modularity(ps, qs, [s["modularity"] for s in stats])

@@ -194,6 +194,40 @@ tec_status tec_ari(tec_graph *g, int k, const int32_t *labels, const int32_t *tr
 tec_status tec_prune_components_batch(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q,
                                       const int64_t *seg_off, int nseg, int32_t *labels_out, int64_t *ncomp_out);
 
+/* Per-threshold statistics of a sweep, the quantities Sec. IV-E plots
+ * against the threshold (Fig. 6), for every graph of a batch (the whole graph
+ * if seg_off is NULL). */
+typedef struct tec_sweep_stat {
+    int64_t ncomp;      /* components */
+    int64_t kept;       /* edges with sim >= p/q (Algorithm 1's survivors) */
+    int64_t largest;    /* vertices of the largest component */
+    int64_t intra;      /* edges of the input graph with both ends in one component */
+    double modularity;  /* Sec. II with the components as communities:
+                           (4 m intra - sum_c vol(c)^2) / (4 m^2), vol(c) the
+                           degree sum of c, from exact integers; 0 if m = 0 */
+} tec_sweep_stat;
+
+/* Statistics of k labelings (device, k x n int32, labels relative to each
+ * graph when seg_off is given, row i the components at p[i]/q[i]: the output
+ * of tec_sweep, or of tec_prune_components_batch at those thresholds).  The
+ * labelings must be nested as a sweep's are (a lower threshold never splits
+ * a component); `intra` is found by binary search over them.  p, q: HOST,
+ * k <= 127, q > 0.  stats_out: device, k x nseg (row-major by threshold).
+ * Per-graph edge counts must stay below 2^31.  Runs tec_support if needed. */
+tec_status tec_sweep_stats(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q, int k,
+                           const int32_t *labels, const int64_t *seg_off, int nseg, tec_sweep_stat *stats_out);
+
+/* The threshold rules of thumb of Sec. IV-E, per graph, from k x nseg
+ * statistics (device) of thresholds p/q (HOST, as given to tec_sweep_stats):
+ *   TEC_RULE_LARGEST_JUMP: visiting the thresholds in decreasing order, the
+ *     one just above the largest increase of the largest component (the
+ *     highest on ties); where it never increases, TEC_RULE_MODULARITY;
+ *   TEC_RULE_MODULARITY: the largest modularity (the lowest threshold on ties).
+ * best_out: device, nseg int32 row indices, on `stream`. */
+typedef enum { TEC_RULE_LARGEST_JUMP = 0, TEC_RULE_MODULARITY = 1 } tec_rule;
+tec_status tec_rule_of_thumb(const tec_sweep_stat *stats, const int64_t *p, const int64_t *q, int k, int nseg,
+                             tec_rule rule, int32_t *best_out, void *stream);
+
 /* For each of nseg graphs, the first of k rows of ari (device, k x nseg, as
  * written by tec_ari) with the highest value: best (device, nseg int32, row
  * index) and, if not NULL, that value (device, nseg float64), on `stream`. */

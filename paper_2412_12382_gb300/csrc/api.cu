@@ -65,7 +65,8 @@ void free_graph_memory(tec_graph *g) {
     void *ptrs[] = {g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->parent, g->tasks,
                     g->flags, g->tile_cnt, g->tile_base, g->bsum, g->uoff, g->ucnt, g->labels, g->lvl, g->best,
                     g->fu, g->fv, g->bucket, g->thr, g->sw_ncomp, g->seg_hist, g->ari_sums,
-                    g->ari_size, g->ari_keys, g->ari_cnt, g->msf_u, g->msf_v, g->msf_k, g->msf_cnt, g->ctr};
+                    g->ari_size, g->ari_keys, g->ari_cnt, g->msf_u, g->msf_v, g->msf_k, g->msf_cnt,
+                    g->st_hist, g->st_sums, g->st_cnt_n, g->st_cnt_v, g->ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (g->ctr_host) cudaFreeHost(g->ctr_host);
@@ -176,6 +177,27 @@ tec_status ensure_seg_scratch(tec_graph *g, int ns) {
     TEC_TRY(dalloc(&g->seg_hist, (int64_t)ns * 64, "per-graph histograms"));
     TEC_TRY(dalloc(&g->ari_sums, (int64_t)ns * 2 * ARI_CHUNK, "per-graph pair sums"));
     g->seg_cap = ns;
+    return TEC_OK;
+}
+
+// Rows sorted by ascending threshold p/q (exact 128-bit comparison), equal
+// thresholds in input order.
+std::vector<int> ascending_rows(const int64_t *p, const int64_t *q, int k) {
+    std::vector<int> order(k);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return (__int128)p[a] * q[b] < (__int128)p[b] * q[a]; });
+    return order;
+}
+
+template <class T>
+tec_status grow(T **buf, int64_t *cap, int64_t need, const char *what) {
+    if (*cap >= need) return TEC_OK;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    TEC_TRY(dalloc(buf, need, what));
+    *cap = need;
     return TEC_OK;
 }
 }  // namespace
@@ -637,6 +659,54 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
         TEC_TRY(read_counters(g));
         for (size_t i = 0; i < hn.size(); ++i) ncomp_out[i] = (int64_t)hn[i];
     }
+    return TEC_OK;
+}
+
+tec_status tec_sweep_stats(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q, int k,
+                           const int32_t *labels, const int64_t *seg_off, int nseg, tec_sweep_stat *stats_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (k < 1 || k > 127) return set_error(TEC_EINVAL, "k must be in [1, 127] (got %d)", k);
+    if (!p || !q || !stats_out) return set_error(TEC_EINVAL, "NULL argument");
+    if (!labels && g->n > 0) return set_error(TEC_EINVAL, "labels is NULL");
+    if (seg_off && nseg < 1) return set_error(TEC_EINVAL, "nseg must be >= 1 with a segment table");
+    bool wide = false;
+    for (int i = 0; i < k; ++i) {
+        TEC_TRY(check_threshold((int)measure, p[i], q[i]));
+        wide = wide || needs_wide(p[i], q[i]);
+    }
+    DeviceGuard dg(g->device);
+    const int ns = seg_off ? nseg : 1;
+    const std::vector<int> order = ascending_rows(p, q, k);
+    std::vector<int64_t> hthr(2 * 127);
+    for (int i = 0; i < k; ++i) {
+        hthr[i] = p[order[i]];
+        hthr[127 + i] = q[order[i]];
+    }
+    if (!g->thr) TEC_TRY(dalloc(&g->thr, 2 * 127, "thresholds"));
+    TEC_TRY(grow(&g->st_hist, &g->st_hist_cap, (int64_t)ns * 2 * (k + 1), "statistics histograms"));
+    TEC_TRY(grow(&g->st_sums, &g->st_sums_cap, (int64_t)k * ns * 3, "statistics sums"));
+    const int64_t cl = std::max<int64_t>(g->n_cap, 1);
+    if (!g->st_cnt_n) TEC_TRY(dalloc(&g->st_cnt_n, 2 * cl, "component sizes"));
+    if (!g->st_cnt_v) TEC_TRY(dalloc(&g->st_cnt_v, 2 * cl, "component volumes"));
+    TEC_CUDA(cudaMemcpyAsync(g->thr, hthr.data(), hthr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
+    TEC_TRY(ensure_support(g));
+    TEC_CUDA(launch_sweep_stats(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, (int)measure, g->thr, g->thr + 127, k,
+                                order.data(), wide, labels, seg_off, nseg, g->st_hist, g->st_cnt_n, g->st_cnt_v, cl,
+                                g->st_sums, stats_out, g->ctr, g->stream));
+    return TEC_OK;
+}
+
+tec_status tec_rule_of_thumb(const tec_sweep_stat *stats, const int64_t *p, const int64_t *q, int k, int nseg,
+                             tec_rule rule, int32_t *best_out, void *stream) {
+    clear_error();
+    if (k < 1 || k > 127 || nseg < 0) return set_error(TEC_EINVAL, "k must be in [1, 127], nseg >= 0");
+    if (!p || !q || (nseg > 0 && (!stats || !best_out))) return set_error(TEC_EINVAL, "NULL argument");
+    if (rule != TEC_RULE_LARGEST_JUMP && rule != TEC_RULE_MODULARITY) return set_error(TEC_EINVAL, "unknown rule");
+    for (int i = 0; i < k; ++i)
+        if (q[i] <= 0) return set_error(TEC_EINVAL, "threshold denominators must be positive");
+    const std::vector<int> order = ascending_rows(p, q, k);
+    TEC_CUDA(launch_rules(stats, k, nseg, order.data(), (int)rule, best_out, (cudaStream_t)stream));
     return TEC_OK;
 }
 

@@ -103,12 +103,6 @@ __device__ __forceinline__ uint64_t hkey(uint64_t key, int bits) {
 
 __device__ __forceinline__ unsigned long long c2(unsigned long long x) { return x * (x - (x > 0)) / 2; }
 
-__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
 // Adds c to a level-tagged counter and returns the count it held at this
 // level (0 if the word carried an older tag).  Within a level a word only
 // goes from an older tag to the current one (by the compare-and-swap here)
@@ -147,26 +141,6 @@ __device__ __forceinline__ int64_t cell_slot(unsigned long long *keys, int bits,
         if (cur == want) return (int64_t)h;
     }
     return -1;
-}
-
-// Groups the valid lanes of a warp by key for one atomic per group: returns
-// a mask of lanes that hold this lane's key (the lane itself at least).  Any
-// grouping by equal keys is exact, because every group computes its pair
-// increment from the count its own atomic returns; so the full (slow) match
-// runs only when neighbouring lanes repeat keys often.  All keys equal
-// (a large component over consecutive vertices) costs one shuffle; mostly
-// distinct keys (singletons, interleaved components) add lane by lane.
-template <typename K>
-__device__ __forceinline__ unsigned key_group(bool valid, K key) {
-    const unsigned lane = lane_id();
-    const unsigned vm = __ballot_sync(0xffffffffu, valid);
-    if (!vm) return 0u;
-    const K k0 = __shfl_sync(0xffffffffu, key, __ffs(vm) - 1);
-    if (__all_sync(0xffffffffu, !valid || key == k0)) return vm;
-    const K up = __shfl_up_sync(0xffffffffu, key, 1);
-    const bool rep = valid && lane > 0 && ((vm >> (lane - 1)) & 1u) && key == up;
-    if (__popc(__ballot_sync(0xffffffffu, rep)) >= 8) return __match_any_sync(0xffffffffu, key) & vm;
-    return 1u << lane;
 }
 
 // Adds the per-lane pair-count increments of a warp to sums[2 s + which]:

@@ -169,6 +169,18 @@ cudaError_t launch_ari(const int32_t *labels, int k, const int32_t *truth, int64
                        unsigned long long *cnt, int64_t tsize, unsigned long long *sums, double *out,
                        unsigned long long *tag, unsigned long long *ctr, cudaStream_t s);
 
+// stats.cu: sweep statistics (thresholds sorted ascending in tp/tq, order[i]
+// = row of the i-th; hist 2 (k+1) per graph, sums 3 per row and graph,
+// cnt_n / cnt_v two arrays of cnt_len >= n each).
+cudaError_t launch_sweep_stats(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
+                               int64_t n, int64_t m, int measure, const int64_t *tp, const int64_t *tq, int k,
+                               const int *order, bool wide, const int32_t *labels, const int64_t *seg_off, int nseg,
+                               unsigned long long *hist, unsigned int *cnt_n, unsigned long long *cnt_v,
+                               int64_t cnt_len, unsigned long long *sums, tec_sweep_stat *out,
+                               unsigned long long *ctr, cudaStream_t s);
+cudaError_t launch_rules(const tec_sweep_stat *stats, int k, int nseg, const int *order, int rule, int32_t *best,
+                         cudaStream_t s);
+
 // cc.cu
 cudaError_t launch_cc_init(int32_t *parent, int64_t n, cudaStream_t s);
 cudaError_t launch_cc_hook(const int64_t *ooff, const int32_t *ocol, const uint32_t *keep,
@@ -209,6 +221,32 @@ constexpr int VCHUNK = 32 * VCHUNK_V;
 // Grid for a persistent vertex pass of 256-thread blocks: enough warps for
 // every chunk, at most 16 blocks per SM.
 unsigned vertex_pass_grid(int64_t n);
+
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Groups the valid lanes of a warp by key for one atomic per group: returns
+// a mask of lanes that hold this lane's key (the lane itself at least).  Any
+// grouping by equal keys is exact, because every group computes its pair
+// increment from the count its own atomic returns; so the full (slow) match
+// runs only when neighbouring lanes repeat keys often.  All keys equal
+// (a large component over consecutive vertices) costs one shuffle; mostly
+// distinct keys (singletons, interleaved components) add lane by lane.
+template <typename K>
+__device__ __forceinline__ unsigned key_group(bool valid, K key) {
+    const unsigned lane = lane_id();
+    const unsigned vm = __ballot_sync(0xffffffffu, valid);
+    if (!vm) return 0u;
+    const K k0 = __shfl_sync(0xffffffffu, key, __ffs(vm) - 1);
+    if (__all_sync(0xffffffffu, !valid || key == k0)) return vm;
+    const K up = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool rep = valid && lane > 0 && ((vm >> (lane - 1)) & 1u) && key == up;
+    if (__popc(__ballot_sync(0xffffffffu, rep)) >= 8) return __match_any_sync(0xffffffffu, key) & vm;
+    return 1u << lane;
+}
 
 // Largest r in [lo, hi] with off[r] <= k (off non-decreasing, off[lo] <= k).
 __device__ __forceinline__ int64_t row_search(const int64_t *off, int64_t lo, int64_t hi, int64_t k) {
@@ -305,6 +343,13 @@ struct tec_graph {
     unsigned long long *ari_keys = nullptr; // 2^bits level-tagged cell keys
     unsigned long long *ari_cnt = nullptr;  // 2^bits level-tagged cell counts
     unsigned long long ari_tag = 0;         // last level tag used in the arrays above
+    // sweep statistics scratch, grown on demand
+    unsigned long long *st_hist = nullptr;  // nseg x 2 (k + 1) level / join-level histograms
+    int64_t st_hist_cap = 0;
+    unsigned long long *st_sums = nullptr;  // k x nseg x 3 root counts, maxima, squared volumes
+    int64_t st_sums_cap = 0;
+    unsigned int *st_cnt_n = nullptr;       // 2 x n_cap vertices per root (two levels in turn)
+    unsigned long long *st_cnt_v = nullptr; // 2 x n_cap degree volume per root
     unsigned long long *ctr = nullptr;      // device counter block
     unsigned long long *ctr_host = nullptr; // pinned mirror for reads
 

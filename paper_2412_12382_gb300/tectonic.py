@@ -73,10 +73,18 @@ SIGNATURES = {
                          ctypes.c_int),
     "tec_picker_thresholds": ([_P, _I64, _P, _P, _P], ctypes.c_int),
     "tec_pick_threshold": ([_P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
+    "tec_sweep_stats": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "tec_rule_of_thumb": ([_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
     "tec_components_noalloc": ([_I64, _I64, _P, _P, _P, _P, _PI64, _P], ctypes.c_int),
 }
 
 NOALLOC_MAX_VERTICES = 4194304
+
+# tec_sweep_stat, field for field
+STAT_DTYPE = np.dtype([("ncomp", "<i8"), ("kept", "<i8"), ("largest", "<i8"), ("intra", "<i8"),
+                       ("modularity", "<f8")])
+RULE_LARGEST_JUMP = 0
+RULE_MODULARITY = 1
 
 
 def components_noalloc(n: int, eu, ev, keep=None, labels=None, stream=None):
@@ -316,6 +324,19 @@ class Graph:
                                 _ptr(seg_off) if seg_off is not None else None, nseg, _ptr(out)))
         return out
 
+    def sweep_stats(self, measure: int, ps, qs, labels, seg_off=None):
+        """Statistics of k nested labelings (k x n CUDA int32, rows at ps[i]/qs[i]):
+        raw device buffer of k x nseg tec_sweep_stat (see stats_numpy)."""
+        torch = _torch()
+        k = len(ps)
+        hp = np.ascontiguousarray(ps, dtype=np.int64)
+        hq = np.ascontiguousarray(qs, dtype=np.int64)
+        nseg = 0 if seg_off is None else seg_off.numel() - 1
+        buf = torch.empty(k * max(nseg, 1) * STAT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        check(self._lib.tec_sweep_stats(self._h, int(measure), _ptr(hp), _ptr(hq), k, _ptr(labels.contiguous()),
+                                        _ptr(seg_off) if seg_off is not None else None, nseg, _ptr(buf)))
+        return buf
+
     def pick_threshold(self, picker, seg_off=None, bf16: bool = True):
         """Learned grid threshold per graph: (p, q) CUDA int64 tensors (nseg, or 1 without segments)."""
         torch = _torch()
@@ -374,6 +395,24 @@ def ari_best(ari, stream=None):
     stream = stream or torch.cuda.current_stream()
     check(load_library().tec_ari_best(_ptr(ari.contiguous()), k, nseg, _ptr(best), _ptr(val), _P(stream.cuda_stream)))
     return best, val
+
+
+def stats_numpy(buf, k: int, nseg: int = 1):
+    """Host copy of a tec_sweep_stats buffer as a (k, nseg) structured array."""
+    return np.frombuffer(buf.cpu().numpy().tobytes(), dtype=STAT_DTYPE).reshape(k, max(nseg, 1))
+
+
+def rule_of_thumb(stats_buf, ps, qs, nseg: int = 1, rule: int = RULE_LARGEST_JUMP, stream=None):
+    """Row picked per graph by a threshold rule of thumb (Sec. IV-E): CUDA int32 tensor."""
+    torch = _require_cuda()
+    k = len(ps)
+    hp = np.ascontiguousarray(ps, dtype=np.int64)
+    hq = np.ascontiguousarray(qs, dtype=np.int64)
+    best = torch.empty(max(nseg, 1), dtype=torch.int32, device="cuda")
+    stream = stream or torch.cuda.current_stream()
+    check(load_library().tec_rule_of_thumb(_ptr(stats_buf), _ptr(hp), _ptr(hq), k, max(nseg, 1), int(rule),
+                                           _ptr(best), _P(stream.cuda_stream)))
+    return best
 
 
 def picker_thresholds(y, stream=None):

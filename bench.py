@@ -212,6 +212,13 @@ def bench_batched_sweep(reps=3):
     [1000, 200000]) as one batch: components at the 64 thresholds b/128 by the
     spanning-forest sweep, against 64 independent prune + components passes."""
     import torch
+    side = torch.cuda.Stream()          # CUDA-graph capture needs a non-default stream
+    with torch.cuda.stream(side):
+        return _bench_batched_sweep(reps)
+
+
+def _bench_batched_sweep(reps):
+    import torch
     from graphgen.gpu import dcsbm_batch_gpu
     from paper_2412_12382_gb300 import TECTONIC, Graph
     from paper_2412_12382_gb300 import picker as PK
@@ -233,11 +240,21 @@ def bench_batched_sweep(reps=3):
             g.prune_components_batch(TECTONIC, p, q, seg, labels=lab, count=False)
 
     ind_ms, _ = _timed(independent, stream, reps)
+    # the same sweep captured once in a CUDA graph and replayed
+    lab_g = None
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg, stream=stream):
+        lab_g, _ = g.sweep(TECTONIC, PK.GRID_P, PK.GRID_Q, seg_off=seg, count=False)
+    graph_ms, _ = _timed(cg.replay, stream, reps + 1)
+    ref, _ = g.sweep(TECTONIC, PK.GRID_P, PK.GRID_Q, seg_off=seg, count=False)
+    same = bool(torch.equal(lab_g, ref))
+    del cg
     m = g.m
     g.free()
     return {"workload": "256 DC-SBM graphs, seeds 1000-1255, n log-uniform in [1e3, 2e5], 64 thresholds b/128",
             "graphs": nseg, "n": int(off.numel() - 1), "m": int(m), "support_ms": sup_ms,
-            "sweep_ms": sweep_ms, "independent_passes_ms": ind_ms, "speedup_vs_independent": ind_ms / sweep_ms,
+            "sweep_ms": sweep_ms, "sweep_cuda_graph_ms": graph_ms, "cuda_graph_labels_match": same,
+            "independent_passes_ms": ind_ms, "speedup_vs_independent": ind_ms / sweep_ms,
             "graphs_per_s": nseg / (sweep_ms / 1e3), "edges_per_s": m / (sweep_ms / 1e3),
             "input_generation_s": gen_s}
 
@@ -286,6 +303,14 @@ def bench_picker(reps=3):
     got = g.ari(plab[None, :], truth, seg)[0]
     ari_all = g.ari(lab_all, truth, seg)
     fixed_level = int(meta.get("eval", {}).get("fixed_level", 8)) - 1
+    # the paper's rules of thumb (Sec. IV-E) on the same sweep, as baselines
+    stats = g.sweep_stats(TECTONIC, PK.GRID_P, PK.GRID_Q, lab_all, seg)
+    cols = torch.arange(nseg, device="cuda")
+    rule_ari = {}
+    for name, rule in (("R1", T.RULE_LARGEST_JUMP), ("R2", T.RULE_MODULARITY)):
+        rows = T.rule_of_thumb(stats, PK.GRID_P, PK.GRID_Q, nseg, rule).long()
+        rule_ari[name] = float(ari_all[rows, cols].mean())
+    stats_ms, _ = _timed(lambda: g.sweep_stats(TECTONIC, PK.GRID_P, PK.GRID_Q, lab_all, seg), stream, 2)
     d = (best_ari - got).cpu().numpy()
     out = {"workload": "500 held-out DC-SBM graphs, seeds 20000-20499, n log-uniform in [1e3, 1e5]",
            "graphs": int(nseg), "n": int(g.n), "m": int(g.m), "picker_ms": picker_ms,
@@ -297,6 +322,8 @@ def bench_picker(reps=3):
            "mean_dARI": float(d.mean()), "p95_dARI": float(np.percentile(d, 95)), "max_dARI": float(d.max()),
            "mean_ARI_picker": float(got.mean()), "mean_ARI_best": float(best_ari.mean()),
            "mean_ARI_fixed": float(ari_all[fixed_level].mean()), "fixed_threshold": f"{fixed_level + 1}/128",
+           "mean_ARI_R1_largest_jump": rule_ari["R1"], "mean_ARI_R2_modularity": rule_ari["R2"],
+           "sweep_stats_ms": stats_ms,
            "inference": "bf16", "trained_on": meta.get("train_seeds"), "epochs_kept": meta.get("epochs_kept")}
     g.free()
     pk.free()

@@ -65,7 +65,7 @@ void free_graph_memory(tec_graph *g) {
     void *ptrs[] = {g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->parent, g->tasks,
                     g->flags, g->tile_cnt, g->tile_base, g->bsum, g->uoff, g->ucnt, g->labels, g->lvl, g->best,
                     g->fu, g->fv, g->bucket, g->thr, g->sw_ncomp, g->seg_hist, g->ari_sums,
-                    g->ari_size, g->ari_keys, g->ari_cnt, g->msf_u, g->msf_v, g->msf_k, g->msf_cnt,
+                    g->ari_size, g->ari_keys, g->ari_cnt, g->msf_u, g->msf_v, g->msf_k, g->msf_cnt, g->msf_changed,
                     g->st_hist, g->st_sums, g->st_cnt_n, g->st_cnt_v, g->ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -616,41 +616,41 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
     const bool list = g->msf_cap > 0;
     int32_t *lu = list ? g->msf_u : nullptr, *lv = list ? g->msf_v : nullptr, *lc = list ? g->msf_cnt : nullptr;
     unsigned long long *lk = list ? g->msf_k : nullptr;
-    TEC_CUDA(cudaMemcpyAsync(g->thr, hthr.data(), hthr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    if (!g->msf_changed) TEC_TRY(dalloc(&g->msf_changed, 64, "forest round flags"));
     TEC_TRY(ensure_support(g));
-    // Boruvka rounds of the maximum spanning forest; the first runs in the level pass
+    // From here on only kernels and memsets on the graph's stream: with the
+    // buffers above allocated and ncomp_out NULL, a caller can capture the
+    // whole sweep in a CUDA graph.
+    TEC_CUDA(launch_store_thresholds(hthr.data(), 2 * k, g->thr, s));
+    // Boruvka rounds of the maximum spanning forest.  The first runs in the
+    // level pass; every round merges each tree that still has a live edge, so
+    // ceil(log2 n) + 1 rounds complete the forest and one more finds nothing.
+    // Rounds after a round that joined nothing return at once.
+    int rounds = 2;
+    while (rounds < 64 && ((int64_t)1 << (rounds - 2)) < g->n) ++rounds;
     g->pruned = g->hooked = false;
     TEC_CUDA(launch_cc_init(g->parent, g->n, s));
     if (g->n > 0) TEC_CUDA(cudaMemsetAsync(g->best, 0, (size_t)g->n * sizeof(unsigned long long), s));
+    TEC_CUDA(cudaMemsetAsync(g->msf_changed, 0, 64 * sizeof(unsigned long long), s));
     TEC_CUDA(launch_levels(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, (int)measure, g->thr, g->thr + k, k, wide,
                            g->lvl, g->best, lu, lv, lk, lc, g->ctr, s));
-    int round = 0;
-    for (; round < 64; ++round) {
-        TEC_TRY(reset_counter(g, C_CHANGED));
+    for (int round = 0; round < rounds; ++round) {
+        const unsigned long long *prev = round > 0 ? g->msf_changed + round - 1 : nullptr;
         if (round > 0)
-            TEC_CUDA(launch_msf_offer(g->ooff, g->ocol, g->lvl, g->n, g->m, g->parent, g->best, lu, lv, lk, lc,
+            TEC_CUDA(launch_msf_offer(g->ooff, g->ocol, g->lvl, g->n, g->m, g->parent, g->best, lu, lv, lk, lc, prev,
                                       g->ctr, s));
-        TEC_CUDA(launch_msf_hook(g->ooff, g->ocol, g->lvl, g->n, g->parent, g->best, g->ctr, s));
-        TEC_TRY(read_counters(g));
-        if (g->ctr_host[C_CHANGED] == 0) break;
+        TEC_CUDA(launch_msf_hook(g->ooff, g->ocol, g->lvl, g->n, g->parent, g->best, prev, g->msf_changed + round,
+                                 g->ctr, s));
     }
-    if (round == 64) return set_error(TEC_ETIMEOUT, "the spanning forest did not converge in 64 rounds");
+    TEC_CUDA(launch_msf_check(g->msf_changed + rounds - 1, g->ctr, s));
     // offline sweep over the forest edges, highest level first
-    TEC_CUDA(launch_forest_buckets(g->ooff, g->ocol, g->lvl, g->n, g->m, k, g->bucket, g->fu, g->fv, s));
-    std::vector<unsigned long long> boff((size_t)k + 2);   // bucket offsets, sized launches per level
-    TEC_CUDA(cudaMemcpyAsync(boff.data(), g->bucket + k + 1, boff.size() * sizeof(unsigned long long),
-                             cudaMemcpyDeviceToHost, s));
+    TEC_CUDA(launch_forest_buckets(g->ooff, g->ocol, g->lvl, g->n, g->m, k, g->bucket, g->fu, g->fv, g->ctr, s));
     TEC_CUDA(launch_cc_init(g->parent, g->n, s));
     TEC_CUDA(cudaMemsetAsync(g->sw_ncomp, 0, (size_t)k * nsl * sizeof(unsigned long long), s));
-    TEC_CUDA(cudaStreamSynchronize(s));
-    if (boff[k + 1] > (unsigned long long)std::max<int64_t>(g->n - 1, 0))
-        return set_error(TEC_EBADGRAPH, "spanning forest has %llu edges for %lld vertices", boff[k + 1],
-                         (long long)g->n);
     for (int L = k; L >= 1; --L) {
         const int dst = order[L - 1];
-        TEC_CUDA(launch_sweep_level(g->fu, g->fv, (int64_t)boff[L], (int64_t)boff[L + 1], g->n, g->parent,
-                                    labels_out + (int64_t)dst * g->n, seg_off, nseg,
-                                    g->sw_ncomp + (int64_t)dst * nsl, g->ctr, s));
+        TEC_CUDA(launch_sweep_level(g->fu, g->fv, g->bucket, k, L, g->n, g->parent, labels_out + (int64_t)dst * g->n,
+                                    seg_off, nseg, g->sw_ncomp + (int64_t)dst * nsl, g->ctr, s));
     }
     if (ncomp_out) {
         std::vector<unsigned long long> hn((size_t)k * nsl);

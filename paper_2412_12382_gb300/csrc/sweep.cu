@@ -19,6 +19,7 @@
 // A batch of graphs is one disjoint union: with a segment table the snapshot
 // writes labels relative to each graph's first vertex and counts components
 // per graph.
+#include <algorithm>
 #include <atomic>
 
 #include "tec_internal.cuh"
@@ -121,71 +122,85 @@ k_levels(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uin
 // only merge, so such an edge never joins two trees again).  Every entry of
 // the region is read before the block's barrier and written after it.
 __global__ void __launch_bounds__(TILE_THREADS)
-k_msf_offer_list(int32_t *lu, int32_t *lv, unsigned long long *lk, int32_t *rcnt, int32_t *parent,
-                 unsigned long long *best) {
-    const int64_t base = (int64_t)blockIdx.x * TILE;
-    const int cnt = rcnt[blockIdx.x];
-    if (cnt == 0) return;                        // uniform over the block
-    int32_t ru[TILE_ITEMS], rv[TILE_ITEMS];
-    unsigned long long key[TILE_ITEMS];
-    unsigned live = 0;
-    int c = 0;
+k_msf_offer_list(int32_t *lu, int32_t *lv, unsigned long long *lk, int32_t *rcnt, int64_t ntiles, int32_t *parent,
+                 unsigned long long *best, const unsigned long long *prev_changed) {
+    if (*prev_changed == 0ull) return;           // forest complete; uniform over the grid
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {   // persistent over tile regions
+        const int64_t base = tile * TILE;
+        const int cnt = rcnt[tile];
+        if (cnt == 0) continue;                  // uniform over the block
+        int32_t ru[TILE_ITEMS], rv[TILE_ITEMS];
+        unsigned long long key[TILE_ITEMS];
+        unsigned live = 0;
+        int c = 0;
 #pragma unroll
-    for (int i = 0; i < TILE_ITEMS; ++i) {
-        const int idx = i * TILE_THREADS + (int)threadIdx.x;
-        ru[i] = rv[i] = 0;
-        key[i] = 0;
-        if (idx >= cnt) continue;
-        const int32_t a = uf_find(parent, lu[base + idx]);
-        const int32_t b = uf_find(parent, lv[base + idx]);
-        if (a == b) continue;
-        key[i] = lk[base + idx];
-        ru[i] = a;
-        rv[i] = b;
-        atomicMax(&best[a], key[i]);
-        atomicMax(&best[b], key[i]);
-        live |= 1u << i;
-        ++c;
-    }
-    int total;
-    int at = block_excl_prefix(c, &total);
+        for (int i = 0; i < TILE_ITEMS; ++i) {
+            const int idx = i * TILE_THREADS + (int)threadIdx.x;
+            ru[i] = rv[i] = 0;
+            key[i] = 0;
+            if (idx >= cnt) continue;
+            const int32_t a = uf_find(parent, lu[base + idx]);
+            const int32_t b = uf_find(parent, lv[base + idx]);
+            if (a == b) continue;
+            key[i] = lk[base + idx];
+            ru[i] = a;
+            rv[i] = b;
+            atomicMax(&best[a], key[i]);
+            atomicMax(&best[b], key[i]);
+            live |= 1u << i;
+            ++c;
+        }
+        int total;
+        int at = block_excl_prefix(c, &total);
 #pragma unroll
-    for (int i = 0; i < TILE_ITEMS; ++i) {
-        if (!((live >> i) & 1u)) continue;
-        lu[base + at] = ru[i];
-        lv[base + at] = rv[i];
-        lk[base + at] = key[i];
-        ++at;
+        for (int i = 0; i < TILE_ITEMS; ++i) {
+            if (!((live >> i) & 1u)) continue;
+            lu[base + at] = ru[i];
+            lv[base + at] = rv[i];
+            lk[base + at] = key[i];
+            ++at;
+        }
+        if (threadIdx.x == 0) rcnt[tile] = total;
+        __syncthreads();                         // the prefix scratch is reused by the next tile
     }
-    if (threadIdx.x == 0) rcnt[blockIdx.x] = total;
 }
 
 // Every edge with L >= 1 between two different trees offers itself to both roots.
 __global__ void __launch_bounds__(TILE_THREADS)
 k_msf_offer(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_t n, int64_t m,
-            int32_t *parent, unsigned long long *best, unsigned long long *ctr) {
-    const int64_t k0 = (int64_t)blockIdx.x * TILE;
-    const int64_t klast = min(k0 + TILE, m) - 1;
-    const int64_t r0 = row_search(ooff, 0, n - 1, k0);
-    const int64_t r1 = row_search(ooff, r0, n - 1, klast);
-    for (int i = 0; i < TILE_ITEMS; ++i) {
-        const int64_t j = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
-        if (j >= m) break;
-        const uint8_t L = lvl[j] & (uint8_t)~FOREST_BIT;
-        if (L == 0) continue;
-        const int32_t u = (int32_t)row_search(ooff, r0, r1, j);
-        const int32_t ru = uf_find(parent, u), rv = uf_find(parent, ocol[j]);
-        if (ru == rv) continue;
-        const uint64_t key = msf_key(L, j);
-        atomicMax(&best[ru], (unsigned long long)key);
-        atomicMax(&best[rv], (unsigned long long)key);
+            int32_t *parent, unsigned long long *best, const unsigned long long *prev_changed,
+            unsigned long long *ctr) {
+    if (*prev_changed == 0ull) return;           // forest complete; uniform over the grid
+    const int64_t ntiles = ceil_div(m, (int64_t)TILE);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t k0 = tile * TILE;
+        const int64_t klast = min(k0 + TILE, m) - 1;
+        const int64_t r0 = row_search(ooff, 0, n - 1, k0);
+        const int64_t r1 = row_search(ooff, r0, n - 1, klast);
+        for (int i = 0; i < TILE_ITEMS; ++i) {
+            const int64_t j = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
+            if (j >= m) break;
+            const uint8_t L = lvl[j] & (uint8_t)~FOREST_BIT;
+            if (L == 0) continue;
+            const int32_t u = (int32_t)row_search(ooff, r0, r1, j);
+            const int32_t ru = uf_find(parent, u), rv = uf_find(parent, ocol[j]);
+            if (ru == rv) continue;
+            const uint64_t key = msf_key(L, j);
+            atomicMax(&best[ru], (unsigned long long)key);
+            atomicMax(&best[rv], (unsigned long long)key);
+        }
     }
 }
 
 // Each root hooks along its heaviest offer; a hook that joins two trees marks a
-// forest edge.  Clears the offers for the next round.
+// forest edge and sets this round's changed flag (one store per block).
+// Clears the offers for the next round.  Skipped when the previous round
+// joined nothing (the forest is complete).
 __global__ void k_msf_hook(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int32_t *parent,
-                           unsigned long long *best, unsigned long long *ctr) {
+                           unsigned long long *best, const unsigned long long *prev_changed,
+                           unsigned long long *changed, unsigned long long *ctr) {
+    if (prev_changed && *prev_changed == 0ull) return;   // uniform over the grid
+    int did = 0;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const unsigned long long key = best[r];
         if (!key) continue;
@@ -194,9 +209,24 @@ __global__ void k_msf_hook(const int64_t *ooff, const int32_t *ocol, uint8_t *lv
         const int32_t u = (int32_t)row_search(ooff, 0, n - 1, j);
         if (uf_link_merged(parent, u, ocol[j], ctr)) {
             lvl[j] |= FOREST_BIT;
-            atomicAdd(&ctr[C_CHANGED], 1ull);
+            did = 1;
         }
     }
+    if (__syncthreads_or(did) && threadIdx.x == 0) *changed = 1ull;
+}
+
+// Flags a forest that was still growing in the last round the sweep allows.
+__global__ void k_msf_check(const unsigned long long *last_changed, unsigned long long *ctr) {
+    if (*last_changed) flag_status(ctr, ST_TIMEOUT);
+}
+
+// Writes the sorted thresholds (p then q, 127 each) from the launch
+// parameters, so a sweep needs no host-to-device copy.
+struct SweepThresholds {
+    int64_t v[2 * 127];
+};
+__global__ void k_store_thresholds(SweepThresholds th, int count, int64_t *dst) {
+    for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = th.v[i];
 }
 
 // Per-level forest-edge counts: a block histogram in shared memory, merged
@@ -215,7 +245,7 @@ __global__ void k_forest_count(const uint8_t *lvl, int64_t m, int k, unsigned lo
 // bucket[0 .. k] are the counts per level; this writes their exclusive scan
 // to bucket[k+1 .. 2k+2] (k+2 offsets, the last one the total) and a copy used
 // as fill cursors to bucket[2k+3 .. 3k+3] (one thread; k <= 127).
-__global__ void k_forest_offsets(unsigned long long *bucket, int k) {
+__global__ void k_forest_offsets(unsigned long long *bucket, int k, int64_t n, unsigned long long *ctr) {
     unsigned long long acc = 0;
     for (int b = 0; b <= k; ++b) {
         bucket[k + 1 + b] = acc;
@@ -223,6 +253,7 @@ __global__ void k_forest_offsets(unsigned long long *bucket, int k) {
         acc += bucket[b];
     }
     bucket[2 * k + 2] = acc;
+    if (acc > (unsigned long long)(n > 0 ? n - 1 : 0)) flag_status(ctr, ST_BADGRAPH);   // a forest has < n edges
 }
 
 // Writes the forest edges of one tile to their level buckets: the tile's
@@ -262,8 +293,10 @@ k_forest_scatter(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, i
     }
 }
 
-__global__ void k_union_bucket(const int32_t *fu, const int32_t *fv, int64_t b0, int64_t b1, int32_t *parent,
-                               unsigned long long *ctr) {
+// Unions level L's bucket of forest edges; the bounds are read on the device.
+__global__ void k_union_bucket(const int32_t *fu, const int32_t *fv, const unsigned long long *bucket, int k, int L,
+                               int32_t *parent, unsigned long long *ctr) {
+    const int64_t b0 = (int64_t)bucket[k + 1 + L], b1 = (int64_t)bucket[k + 1 + L + 1];
     for (int64_t e = b0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < b1; e += (int64_t)gridDim.x * blockDim.x)
         uf_link(parent, fu[e], fv[e], ctr);
 }
@@ -378,29 +411,51 @@ cudaError_t launch_levels(const int64_t *ooff, const int32_t *ocol, const int32_
 
 cudaError_t launch_msf_offer(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int64_t m,
                              int32_t *parent, unsigned long long *best, int32_t *lu, int32_t *lv,
-                             unsigned long long *lk, int32_t *rcnt, unsigned long long *ctr, cudaStream_t s) {
+                             unsigned long long *lk, int32_t *rcnt, const unsigned long long *prev_changed,
+                             unsigned long long *ctr, cudaStream_t s) {
     if (m <= 0 || n <= 0) return cudaSuccess;
-    if (lu) k_msf_offer_list<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(lu, lv, lk, rcnt, parent, best);
-    else k_msf_offer<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, lvl, n, m, parent, best, ctr);
+    // persistent grids: a round after the forest is complete costs one tiny launch
+    const int64_t ntiles = ceil_div(m, (int64_t)TILE);
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)vertex_pass_grid(int64_t(1) << 40) / 2);
+    if (lu)
+        k_msf_offer_list<<<grid, TILE_THREADS, 0, s>>>(lu, lv, lk, rcnt, ntiles, parent, best, prev_changed);
+    else
+        k_msf_offer<<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, lvl, n, m, parent, best, prev_changed, ctr);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_msf_hook(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int32_t *parent,
-                            unsigned long long *best, unsigned long long *ctr, cudaStream_t s) {
+                            unsigned long long *best, const unsigned long long *prev_changed,
+                            unsigned long long *changed, unsigned long long *ctr, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_msf_hook<<<grid_for(n), 256, 0, s>>>(ooff, ocol, lvl, n, parent, best, ctr);
+    k_msf_hook<<<vertex_pass_grid(n), 256, 0, s>>>(ooff, ocol, lvl, n, parent, best, prev_changed, changed, ctr);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_msf_check(const unsigned long long *last_changed, unsigned long long *ctr, cudaStream_t s) {
+    k_msf_check<<<1, 1, 0, s>>>(last_changed, ctr);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_thresholds(const int64_t *sorted_pq, int count, int64_t *dst, cudaStream_t s) {
+    SweepThresholds th{};
+    for (int i = 0; i < count && i < 2 * 127; ++i) th.v[i] = sorted_pq[i];
+    k_store_thresholds<<<1, 256, 0, s>>>(th, count, dst);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_forest_buckets(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_t n, int64_t m,
-                                  int k, unsigned long long *bucket, int32_t *fu, int32_t *fv, cudaStream_t s) {
+                                  int k, unsigned long long *bucket, int32_t *fu, int32_t *fv, unsigned long long *ctr,
+                                  cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(bucket, 0, (size_t)(k + 1) * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const int64_t cblocks = ceil_div(m, 4096);
     if (m > 0) k_forest_count<<<(unsigned)(cblocks < 152 * 16 ? cblocks : 152 * 16), 256, 0, s>>>(lvl, m, k, bucket);
-    k_forest_offsets<<<1, 1, 0, s>>>(bucket, k);
+    k_forest_offsets<<<1, 1, 0, s>>>(bucket, k, n, ctr);
     if (m > 0)
         k_forest_scatter<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, lvl, n, m, k, bucket, fu, fv);
     count_launches(m > 0 ? 3 : 1);
@@ -415,19 +470,13 @@ cudaError_t launch_snapshot(int32_t *parent, int64_t n, int32_t *labels, const i
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_level(const int32_t *fu, const int32_t *fv, int64_t b0, int64_t b1, int64_t n,
-                               int32_t *parent, int32_t *labels, const int64_t *seg_off, int nseg,
+cudaError_t launch_sweep_level(const int32_t *fu, const int32_t *fv, const unsigned long long *bucket, int k, int L,
+                               int64_t n, int32_t *parent, int32_t *labels, const int64_t *seg_off, int nseg,
                                unsigned long long *ncomp, unsigned long long *ctr, cudaStream_t s) {
-    int launched = 0;
-    if (b1 > b0) {
-        k_union_bucket<<<grid_for(b1 - b0), 256, 0, s>>>(fu, fv, b0, b1, parent, ctr);
-        ++launched;
-    }
-    if (n > 0) {
-        k_snapshot<<<vertex_pass_grid(n), 256, 0, s>>>(parent, n, labels, seg_off, nseg, ncomp);
-        ++launched;
-    }
-    count_launches(launched);
+    if (n <= 0) return cudaSuccess;
+    k_union_bucket<<<vertex_pass_grid(n), 256, 0, s>>>(fu, fv, bucket, k, L, parent, ctr);
+    k_snapshot<<<vertex_pass_grid(n), 256, 0, s>>>(parent, n, labels, seg_off, nseg, ncomp);
+    count_launches(2);
     return cudaGetLastError();
 }
 

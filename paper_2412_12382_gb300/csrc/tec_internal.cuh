@@ -135,18 +135,27 @@ cudaError_t launch_levels(const int64_t *ooff, const int32_t *ocol, const int32_
                           int64_t n, int64_t m, int measure, const int64_t *tp, const int64_t *tq, int k, bool wide,
                           uint8_t *lvl, unsigned long long *best, int32_t *lu, int32_t *lv, unsigned long long *lk,
                           int32_t *rcnt, unsigned long long *ctr, cudaStream_t s);
-// A later Boruvka round's offers: from the live-edge list if lu != nullptr, else from the CSR.
+// A later Boruvka round's offers: from the live-edge list if lu != nullptr,
+// else from the CSR; nothing when *prev_changed is 0 (the forest is complete).
 cudaError_t launch_msf_offer(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int64_t m,
                              int32_t *parent, unsigned long long *best, int32_t *lu, int32_t *lv,
-                             unsigned long long *lk, int32_t *rcnt, unsigned long long *ctr, cudaStream_t s);
-// Hooks every root along its heaviest offer and clears the offers.
+                             unsigned long long *lk, int32_t *rcnt, const unsigned long long *prev_changed,
+                             unsigned long long *ctr, cudaStream_t s);
+// Hooks every root along its heaviest offer, clears the offers and sets
+// *changed when a tree grew; nothing when prev_changed is set and 0.
 cudaError_t launch_msf_hook(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int32_t *parent,
-                            unsigned long long *best, unsigned long long *ctr, cudaStream_t s);
+                            unsigned long long *best, const unsigned long long *prev_changed,
+                            unsigned long long *changed, unsigned long long *ctr, cudaStream_t s);
+// Flags TEC_ETIMEOUT if the last allowed round still grew the forest.
+cudaError_t launch_msf_check(const unsigned long long *last_changed, unsigned long long *ctr, cudaStream_t s);
+// Stores count int64 values (sorted p then q) to dst from the launch parameters.
+cudaError_t launch_store_thresholds(const int64_t *sorted_pq, int count, int64_t *dst, cudaStream_t s);
 cudaError_t launch_forest_buckets(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_t n, int64_t m,
-                                  int k, unsigned long long *bucket, int32_t *fu, int32_t *fv, cudaStream_t s);
-// Unions the forest edges fu/fv[b0, b1) (one level's bucket), then snapshots the labels.
-cudaError_t launch_sweep_level(const int32_t *fu, const int32_t *fv, int64_t b0, int64_t b1, int64_t n,
-                               int32_t *parent, int32_t *labels, const int64_t *seg_off, int nseg,
+                                  int k, unsigned long long *bucket, int32_t *fu, int32_t *fv, unsigned long long *ctr,
+                                  cudaStream_t s);
+// Unions level L's bucket (bounds read on the device), then snapshots the labels.
+cudaError_t launch_sweep_level(const int32_t *fu, const int32_t *fv, const unsigned long long *bucket, int k, int L,
+                               int64_t n, int32_t *parent, int32_t *labels, const int64_t *seg_off, int nseg,
                                unsigned long long *ncomp, unsigned long long *ctr, cudaStream_t s);
 
 cudaError_t launch_snapshot(int32_t *parent, int64_t n, int32_t *labels, const int64_t *seg_off, int nseg,
@@ -329,6 +338,7 @@ struct tec_graph {
     unsigned long long *msf_k = nullptr;  // live-edge list: edge keys
     int32_t *msf_cnt = nullptr;           // live entries per tile region
     int64_t msf_cap = 0;                  // entries allocated (0: no list, rounds rescan the CSR)
+    unsigned long long *msf_changed = nullptr;  // 64 per-round "a tree grew" flags
     int32_t *fu = nullptr, *fv = nullptr; // n: forest edges bucketed by level
     unsigned long long *bucket = nullptr; // 3k+4 bucket counts / offsets / cursors
     int64_t *thr = nullptr;         // 2 * 128 sorted thresholds (p then q)

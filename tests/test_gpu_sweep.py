@@ -86,3 +86,35 @@ def test_sweep_then_prune_components_still_agree(tec):
         cl, cn = g.components()
         assert cn == nc[i] and np.array_equal(cl.cpu().numpy(), lab[i].cpu().numpy())
     g.free()
+
+
+def test_sweep_captured_in_a_cuda_graph(tec):
+    """With its buffers allocated and no host read-back, tec_sweep issues only
+    kernels and memsets on the graph's stream: captured once into a CUDA
+    graph, every replay recomputes the same labels."""
+    import torch
+    from graphgen.batch import disjoint_union
+    from graphgen.dcsbm import dcsbm_csr
+    graphs = [dcsbm_csr(s, 500, 4000)[:2] for s in range(41000, 41006)]
+    off, col, seg = disjoint_union(graphs)
+    ps, qs = list(range(1, 65)), [128] * 64
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        g = tec.Graph(torch.from_numpy(off).cuda(), torch.from_numpy(col).cuda())
+        segd = torch.from_numpy(seg).cuda()
+        ref, _ = g.sweep(O.TECTONIC, ps, qs, seg_off=segd, count=False)   # allocates the sweep buffers
+    s.synchronize()
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg, stream=s):
+        lab, _ = g.sweep(O.TECTONIC, ps, qs, seg_off=segd, count=False)
+    for _ in range(2):
+        lab.fill_(-1)
+        cg.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(lab, ref)
+    labh = lab.cpu().numpy()
+    for i, (go, gc) in enumerate(graphs[:2]):
+        ol, _ = O.sweep(go, gc, O.TECTONIC, ps, qs)
+        assert np.array_equal(labh[:, seg[i]:seg[i + 1]], ol)
+    g.sync()
+    g.free()

@@ -160,7 +160,13 @@ tec_status tec_components(tec_graph *g, int32_t *labels_out, int64_t *ncomp_out)
  * disjoint union: seg_off (device, nseg+1 int64 vertex offsets of the graphs,
  * or NULL) makes every label relative to its graph's first vertex, and
  * ncomp_out (HOST, may be NULL; waits) receives k x nseg component counts (k
- * counts without segments).  Replaces the last prune's mask state. */
+ * counts without segments).  Replaces the last prune's mask state.  Without
+ * ncomp_out the call does not wait: device-side errors (a forest still
+ * growing after ceil(log2 n) + 2 Boruvka rounds, TEC_ETIMEOUT; a malformed
+ * forest, TEC_EBADGRAPH) are reported by the next call that waits.  Once a
+ * first call has allocated the sweep's buffers (and the triangle counts
+ * exist), a call without ncomp_out issues only kernels and memsets on the
+ * graph's stream and can be captured in a CUDA graph. */
 tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q, int k,
                      const int64_t *seg_off, int nseg, int32_t *labels_out, int64_t *ncomp_out);
 

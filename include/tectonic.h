@@ -253,6 +253,16 @@ tec_status tec_full_pass_host(tec_graph *g, const int64_t *row_off_host, const i
                               int64_t n, int64_t nnz, tec_measure measure, int64_t p, int64_t q,
                               int32_t *labels_host, int64_t *ncomp_out);
 
+/* Core staging of the triangle counts (on by default).  Vertices of degree
+ * >= D, D the smallest power of two leaving at most 2^20 of them, get dense
+ * codes in id order, and a copy of the oriented columns holds those codes
+ * (4 bytes per edge).  Centres of degree >= D then stage their out-rows as
+ * exact bitmaps over the codes: no false positives and no positive queue.
+ * Disabling it frees no memory but skips the copy and stages every centre by
+ * hashing; the counts are identical either way.  The next call that needs the
+ * triangle counts recomputes them. */
+tec_status tec_set_core_staging(tec_graph *g, int enable);
+
 /* Instrumentation: number of kernels this library has launched in this
  * process so far (all graphs, all devices). */
 long long tec_launch_count(void);

@@ -66,6 +66,7 @@ void free_graph_memory(tec_graph *g) {
                     g->flags, g->tile_cnt, g->tile_base, g->bsum, g->uoff, g->ucnt, g->labels, g->lvl, g->best,
                     g->fu, g->fv, g->bucket, g->thr, g->sw_ncomp, g->seg_hist, g->ari_sums,
                     g->ari_size, g->ari_keys, g->ari_cnt, g->msf_u, g->msf_v, g->msf_k, g->msf_cnt, g->msf_changed,
+                    g->core_of, g->pv2, g->ctasks, g->core_tc, g->core_hist,
                     g->st_hist, g->st_sums, g->st_cnt_n, g->st_cnt_v, g->ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -108,8 +109,39 @@ tec_status ensure_oriented(tec_graph *g) {
 tec_status ensure_support(tec_graph *g) {
     TEC_TRY(ensure_oriented(g));
     if (g->supported) return TEC_OK;
+    // core staging buffers: allocated once; without the memory the bitmap
+    // kernel is skipped and every block visit uses the hashed staging
+    if (g->core_state == 0 && g->core_enabled) {
+        const int64_t tiles = ceil_div(std::max<int64_t>(g->n_cap, 1), (int64_t)TILE);
+        if (dalloc(&g->core_of, std::max<int64_t>(g->n_cap, 1), "core codes") != TEC_OK ||
+            dalloc(&g->pv2, g->m_cap + 4, "core-coded columns") != TEC_OK ||
+            dalloc(&g->ctasks, g->task_cap, "core visits") != TEC_OK ||
+            dalloc(&g->core_tc, 2 * tiles + 64, "core tile counts") != TEC_OK ||
+            dalloc(&g->core_hist, 36, "degree histogram") != TEC_OK) {
+            void *part[] = {g->core_of, g->pv2, g->ctasks, g->core_tc, g->core_hist};
+            for (void *q2 : part)
+                if (q2) cudaFree(q2);
+            g->core_of = nullptr;
+            g->pv2 = nullptr;
+            g->ctasks = nullptr;
+            g->core_tc = nullptr;
+            g->core_hist = nullptr;
+            g->core_state = -1;
+            clear_error();
+        } else {
+            g->core_state = 1;
+        }
+    }
+    const bool core = g->core_state > 0 && g->core_enabled;
+    if (core) {
+        const int64_t tiles = ceil_div(std::max<int64_t>(g->n, 1), (int64_t)TILE);
+        TEC_CUDA(launch_core_labels(g->deg, g->n, g->ocol, g->m, g->core_hist,
+                                    reinterpret_cast<long long *>(g->core_hist + 33), g->core_tc,
+                                    g->core_tc + tiles + 32, g->bsum, g->core_of, g->pv2, g->stream));
+    }
     TEC_CUDA(launch_support(g->off, g->col, g->flags, g->ooff, g->ocol, g->n, g->m, g->t, g->tasks, g->task_cap,
-                            g->ctr, g->num_sms, g->stream));
+                            g->ctr, g->num_sms, g->stream, core ? g->pv2 : nullptr, core ? g->core_of : nullptr,
+                            core ? g->ctasks : nullptr));
     g->supported = true;
     g->pruned = g->hooked = false;
     return TEC_OK;
@@ -739,6 +771,16 @@ tec_status tec_prune_components_batch(tec_graph *g, tec_measure measure, const i
                                  cudaMemcpyDeviceToHost, g->stream));
         TEC_TRY(read_counters(g));
         for (int i = 0; i < nseg; ++i) ncomp_out[i] = (int64_t)hn[i];
+    }
+    return TEC_OK;
+}
+
+tec_status tec_set_core_staging(tec_graph *g, int enable) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if ((enable != 0) != g->core_enabled) {
+        g->core_enabled = enable != 0;
+        g->supported = g->pruned = g->hooked = false;   // counts are recomputed by the other path
     }
     return TEC_OK;
 }

@@ -67,42 +67,48 @@ __device__ __forceinline__ int64_t visit_len(int64_t du) {
     return v < 256 ? 256 : (v > 65536 ? 65536 : v);
 }
 
-// One thread per vertex: emits the visits of centre c (warp list from the
-// front of tasks[], block list from the back).
+// One thread per vertex: emits the visits of centre c: the warp list from the
+// front of tasks[], the block list from its back, and block visits of core
+// centres (core_of[c] >= 0, when core_of is given) to ctasks[].
 __global__ void k_make_visits(const int64_t *off, const int64_t *ooff, int64_t n, uint64_t *tasks, int64_t cap,
-                              unsigned long long *ctr) {
+                              const int32_t *core_of, uint64_t *ctasks, unsigned long long *ctr) {
     if (graph_bad(ctr)) return;
     const unsigned lane = lane_id();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t c = base + threadIdx.x;
         int64_t du = 0, deg = 0;
+        bool core = false;
         if (c < n) {
             du = ooff[c + 1] - ooff[c];
             deg = off[c + 1] - off[c];
+            core = core_of && du > W_MAX && core_of[c] >= 0;
         }
         // V-mode candidates exist only if c has in-neighbours
         const int64_t ncand = du > 0 ? du + (deg > du ? deg : 0) : 0;
         const int64_t cnt = ncand > 0 ? ceil_div(ncand, visit_len(du)) : 0;
         const bool small = du <= W_MAX;
-        const int64_t my_w = small ? cnt : 0, my_b = small ? 0 : cnt;
-        int64_t sw = my_w, sb = my_b;          // inclusive warp scans
+        const int64_t my_w = small ? cnt : 0, my_b = (small || core) ? 0 : cnt, my_c = core ? cnt : 0;
+        int64_t sw = my_w, sb = my_b, sc = my_c;   // inclusive warp scans
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int64_t yw = __shfl_up_sync(FULL, sw, o), yb = __shfl_up_sync(FULL, sb, o);
-            if ((int)lane >= o) { sw += yw; sb += yb; }
+            const int64_t yc = __shfl_up_sync(FULL, sc, o);
+            if ((int)lane >= o) { sw += yw; sb += yb; sc += yc; }
         }
-        unsigned long long bw = 0, bb = 0;
+        unsigned long long bw = 0, bb = 0, bc = 0;
         if (lane == 31) {
             if (sw) bw = atomicAdd(&ctr[C_NWTASK], (unsigned long long)sw);
             if (sb) bb = atomicAdd(&ctr[C_NBTASK], (unsigned long long)sb);
+            if (sc) bc = atomicAdd(&ctr[C_NCTASK], (unsigned long long)sc);
         }
         bw = __shfl_sync(FULL, bw, 31);
         bb = __shfl_sync(FULL, bb, 31);
-        int64_t at = small ? (int64_t)bw + sw - my_w : (int64_t)bb + sb - my_b;
+        bc = __shfl_sync(FULL, bc, 31);
+        int64_t at = small ? (int64_t)bw + sw - my_w : core ? (int64_t)bc + sc - my_c : (int64_t)bb + sb - my_b;
         for (int64_t i = 0; i < cnt; ++i, ++at) {
-            const int64_t slot = small ? at : cap - 1 - at;
-            if (slot >= 0 && slot < cap) tasks[slot] = ((uint64_t)c << 32) | (uint64_t)i;
+            const int64_t slot = (small || core) ? at : cap - 1 - at;
+            if (slot >= 0 && slot < cap) (core ? ctasks : tasks)[slot] = ((uint64_t)c << 32) | (uint64_t)i;
             else flag_status(ctr, ST_BADGRAPH);
         }
     }
@@ -281,6 +287,63 @@ __device__ __forceinline__ void probe_step(int32_t w, int64_t k, int slot, int32
     }
 }
 
+// Membership policy of the hashed staging: filter test, queue, directory.
+struct FilterSet {
+    Staged S;
+    __device__ __forceinline__ void probe(int32_t w, int64_t k, int slot, int32_t cval, uint32_t *t,
+                                          WarpScratch &ws, int &qn) const {
+        probe_step(w, k, slot, cval, S, t, ws, qn);
+    }
+    __device__ __forceinline__ void finish(uint32_t *t, WarpScratch &ws, int &qn) const {
+        if (qn) drain(ws, qn, S, t);
+        qn = 0;
+    }
+};
+
+// ------------------------------------------------------------------ core staging
+//
+// Vertices of degree >= D are numbered 0 .. K-1 in id order (core codes; D is
+// the smallest power of two with K <= 2^20), and pv2[j] is the code of ocol[j]
+// or -1.  Every id of N+(c) ranks above c, so has degree >= deg(c): for a
+// centre of degree >= D all of N+(c) is core, and a chunk of it is staged as
+// an exact bitmap over core codes.  A probe is then one shared load and a bit
+// test (a non-core id misses at once); a hit's position in the chunk is the
+// position of its word's first member, pref[word], plus the members below it
+// in the word (codes follow ids, so bit order is position order).  There are
+// no false positives and no queue: hits are credited where they are found.
+constexpr int CORE_BITS = 20;
+constexpr int64_t CORE_CAP = int64_t(1) << CORE_BITS;
+constexpr int C_WORDS = (int)(CORE_CAP / 64);        // bitmap words
+constexpr int C_CHUNK = 8192;                          // staged ids per chunk (positions fit 16 bits)
+constexpr int C_THREADS = 1024;
+constexpr int C_WARPS = C_THREADS / 32;
+constexpr size_t C_SMEM = (size_t)C_WORDS * 8 + (size_t)C_WORDS * 2 + (size_t)C_CHUNK * 4;
+
+struct CoreScratch {
+    uint32_t rowhits[32];  // hits per candidate of the batch
+    int64_t jpos[32];      // V-mode: position of c in the candidate's row
+};
+
+struct CoreSet {
+    const unsigned long long *bm;   // C_WORDS words, members of the staged chunk
+    const uint16_t *pref;           // per word holding members: position of its first member
+    uint32_t *cnt;                  // per position: triangles on c -> member
+    __device__ __forceinline__ void probe(int32_t w, int64_t k, int slot, int32_t cval, uint32_t *t,
+                                          CoreScratch &ws, int &) const {
+        if (w < 0) return;
+        if (w == cval) ws.jpos[slot] = k;
+        const unsigned long long word = bm[w >> 6];
+        const unsigned sh = (unsigned)w & 63u;
+        if ((word >> sh) & 1ull) {
+            const int p = (int)pref[w >> 6] + __popcll(word & ((1ull << sh) - 1ull));
+            atomicAdd(&cnt[p], 1u);                   // c -> w
+            atomicAdd(&t[k], 1u);                     // x -> w
+            atomicAdd(&ws.rowhits[slot], 1u);         // x -> c or c -> x, credited per row
+        }
+    }
+    __device__ __forceinline__ void finish(uint32_t *, CoreScratch &, int &) const {}
+};
+
 // One warp processes candidates q0 .. min(q0 + 32, qend) - 1 of centre c
 // against the staged chunk S.  Rows longer than SHORT_ROW are read one at a
 // time by the whole warp; the shorter ones are laid end to end over the lanes
@@ -288,15 +351,17 @@ __device__ __forceinline__ void probe_step(int32_t w, int64_t k, int slot, int32
 // rows' start offsets).  U-mode row hits are credited to c -> x through
 // S.cnt[q] when uv_local (the whole N+(c) is staged) or through t otherwise;
 // V-mode row hits to x -> c at the position of c in N+(x).
+template <class Set, class Scratch>
 __device__ __forceinline__ void process_batch(const int64_t *off, const int32_t *col, const uint32_t *flags,
-                                              const int64_t *ooff, const int32_t *ocol, uint32_t *t, int32_t c,
-                                              int64_t cb, int64_t du, int64_t q0, int64_t qend, bool chunked,
-                                              const Staged &S, bool uv_local, WarpScratch &ws,
+                                              const int64_t *ooff, const int32_t *ocol, const int32_t *pv,
+                                              uint32_t *t, int32_t c, int32_t cval, int64_t cb, int64_t du,
+                                              int64_t q0, int64_t qend, bool chunked, int32_t lo_id, int32_t hi_id,
+                                              const Set &S, uint32_t *scnt, bool uv_local, Scratch &ws,
                                               unsigned long long *ctr) {
     const unsigned lane = lane_id();
     const int64_t q = q0 + lane;
     Cand cd{0, -1, 0, false};
-    if (q < qend) cd = load_cand(off, col, flags, ooff, ocol, c, cb, du, q, chunked, S.a[0], S.a[S.cl - 1]);
+    if (q < qend) cd = load_cand(off, col, flags, ooff, ocol, c, cb, du, q, chunked, lo_id, hi_id);
     ws.rowhits[lane] = 0u;
     ws.jpos[lane] = cd.jpos;
     __syncwarp();
@@ -307,14 +372,14 @@ __device__ __forceinline__ void process_batch(const int64_t *off, const int32_t 
     unsigned pf = todo;
     {
         const unsigned rank = __popc(todo & ((1u << lane) - 1u));
-        if (((todo >> lane) & 1u) && rank < PF_DEPTH) l2_prefetch_ids(ocol, cd.rs, cd.len);
+        if (((todo >> lane) & 1u) && rank < PF_DEPTH) l2_prefetch_ids(pv, cd.rs, cd.len);
         for (int i = 0; i < PF_DEPTH && pf; ++i) pf &= pf - 1;
     }
     while (todo) {
         const int src = __ffs(todo) - 1;
         todo &= todo - 1;
         if (pf) {
-            if ((int)lane == __ffs(pf) - 1) l2_prefetch_ids(ocol, cd.rs, cd.len);
+            if ((int)lane == __ffs(pf) - 1) l2_prefetch_ids(pv, cd.rs, cd.len);
             pf &= pf - 1;
         }
         const int64_t rs = __shfl_sync(FULL, cd.rs, src);
@@ -324,11 +389,10 @@ __device__ __forceinline__ void process_batch(const int64_t *off, const int32_t 
 #pragma unroll
             for (int j = 0; j < UNROLL; ++j) {   // all loads issued before any is used
                 const int i = base + 32 * j + (int)lane;
-                w[j] = i < len ? __ldg(&ocol[rs + i]) : -1;
+                w[j] = i < len ? __ldg(&pv[rs + i]) : -1;
             }
 #pragma unroll
-            for (int j = 0; j < UNROLL; ++j)
-                probe_step(w[j], rs + base + 32 * j + (int)lane, src, c, S, t, ws, qn);
+            for (int j = 0; j < UNROLL; ++j) S.probe(w[j], rs + base + 32 * j + (int)lane, src, cval, t, ws, qn);
         }
     }
     // short rows, packed end to end
@@ -358,17 +422,17 @@ __device__ __forceinline__ void process_batch(const int64_t *off, const int32_t 
             const int pst = __shfl_sync(FULL, sstart, p);
             own[j] = p;
             kk[j] = prs + (e - pst);
-            w[j] = e < stotal ? __ldg(&ocol[kk[j]]) : -1;
+            w[j] = e < stotal ? __ldg(&pv[kk[j]]) : -1;
         }
 #pragma unroll
-        for (int j = 0; j < UNROLL; ++j) probe_step(w[j], kk[j], own[j], c, S, t, ws, qn);
+        for (int j = 0; j < UNROLL; ++j) S.probe(w[j], kk[j], own[j], cval, t, ws, qn);
     }
     __syncwarp();
-    if (qn) drain(ws, qn, S, t);
+    S.finish(t, ws, qn);
     const uint32_t hits = ws.rowhits[lane];
     if (hits) {
         if (q < du) {
-            if (uv_local) atomicAdd(&S.cnt[q], hits);       // c -> x (whole N+(c) staged)
+            if (uv_local) atomicAdd(&scnt[q], hits);        // c -> x (whole N+(c) staged)
             else atomicAdd(&t[cb + q], hits);               // c -> x
         } else {
             const int64_t jp = ws.jpos[lane];
@@ -413,7 +477,8 @@ __device__ __forceinline__ void warp_visit(const int64_t *off, const int32_t *co
     index_staged(S, filt, dir, W_DIR, (int)lane, 32);
     __syncwarp();
     for (int64_t q0 = qbeg; q0 < qend; q0 += 32)
-        process_batch(off, col, flags, ooff, ocol, t, c, cb, du, q0, qend, false, S, true, ws, ctr);
+        process_batch(off, col, flags, ooff, ocol, ocol, t, c, c, cb, du, q0, qend, false, S.a[0], S.a[S.cl - 1],
+                      FilterSet{S}, S.cnt, true, ws, ctr);
     __syncwarp();
     for (int i = (int)lane; i < du; i += 32) {
         const uint32_t cv = s_cnt[i];
@@ -481,8 +546,8 @@ k_support(const int64_t *off, const int32_t *col, const uint32_t *flags, const i
                 if (lane == 0) b = atomicAdd(&s_next, 32);
                 b = __shfl_sync(FULL, b, 0);
                 if (qbeg + b >= qend) break;
-                process_batch(off, col, flags, ooff, ocol, t, c, cb, du, qbeg + b, qend, chunked, S, false, ws,
-                              ctr);
+                process_batch(off, col, flags, ooff, ocol, ocol, t, c, c, cb, du, qbeg + b, qend, chunked, S.a[0],
+                              S.a[S.cl - 1], FilterSet{S}, S.cnt, false, ws, ctr);
             }
             __syncthreads();
             for (int i = threadIdx.x; i < cl; i += B_THREADS) {
@@ -511,6 +576,169 @@ __global__ void k_reset_support_counters(unsigned long long *ctr) {
     ctr[C_NBTASK] = 0;
     ctr[C_NEXT] = 0;
     ctr[C_NEXTW] = 0;
+    ctr[C_NCTASK] = 0;
+    ctr[C_NEXTC] = 0;
+}
+
+// ------------------------------------------------------------------ core labels
+
+// hist[b] = vertices of degree in [2^b, 2^(b+1)) (b < 32); hist[32] = degree 0.
+__global__ void k_degree_log_hist(const int32_t *deg, int64_t n, unsigned long long *hist) {
+    __shared__ unsigned int h[33];
+    if (threadIdx.x < 33) h[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int d = deg[v];
+        atomicAdd(&h[d > 0 ? 31 - __clz(d) : 32], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 33 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], (unsigned long long)h[threadIdx.x]);
+}
+
+// meta[0] = D, the smallest power of two with at most CORE_CAP vertices of
+// degree >= D (0: no core); meta[1] = that count K.
+__global__ void k_core_pick(const unsigned long long *hist, long long *meta) {
+    unsigned long long k = 0;
+    int best = -1;
+    unsigned long long kb = 0;
+    for (int b = 31; b >= 0; --b) {
+        k += hist[b];
+        if (k > (unsigned long long)CORE_CAP) break;
+        best = b;
+        kb = k;
+    }
+    meta[0] = (best >= 0 && kb > 0) ? (1ll << best) : 0ll;
+    meta[1] = (best >= 0) ? (long long)kb : 0ll;
+}
+
+// Per TILE of vertices: the number of core vertices (degree >= D).
+__global__ void k_core_count(const int32_t *deg, int64_t n, const long long *meta, int64_t *tcnt) {
+    const long long D = meta[0];
+    const int64_t v0 = (int64_t)blockIdx.x * TILE;
+    int c = 0;
+    for (int i = 0; i < TILE_ITEMS; ++i) {
+        const int64_t v = v0 + (int64_t)i * TILE_THREADS + threadIdx.x;
+        if (v < n && D > 0 && deg[v] >= D) ++c;
+    }
+    c = warp_sum(c);
+    __shared__ int s_c[TILE_THREADS / 32];
+    if (lane_id() == 0) s_c[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < TILE_THREADS / 32; ++w) t += s_c[w];
+        tcnt[blockIdx.x] = t;
+    }
+}
+
+// core_of[v] = rank of v among the core vertices in id order, or -1.
+__global__ void k_core_fill(const int32_t *deg, int64_t n, const long long *meta, const int64_t *tbase,
+                            int32_t *core_of) {
+    const long long D = meta[0];
+    const int64_t v0 = (int64_t)blockIdx.x * TILE;
+    __shared__ int s_w[TILE_THREADS / 32];
+    int64_t run = tbase[blockIdx.x];
+    for (int i = 0; i < TILE_ITEMS; ++i) {     // one row of TILE_THREADS vertices at a time, in id order
+        const int64_t v = v0 + (int64_t)i * TILE_THREADS + threadIdx.x;
+        const bool is_core = v < n && D > 0 && deg[v] >= D;
+        const unsigned b = __ballot_sync(FULL, is_core);
+        if (lane_id() == 0) s_w[threadIdx.x >> 5] = __popc(b);
+        __syncthreads();
+        int before = 0, row = 0;
+        for (int w = 0; w < TILE_THREADS / 32; ++w) {
+            before += w < (int)(threadIdx.x >> 5) ? s_w[w] : 0;
+            row += s_w[w];
+        }
+        if (v < n) core_of[v] = is_core ? (int32_t)(run + before + __popc(b & ((1u << lane_id()) - 1u))) : -1;
+        run += row;
+        __syncthreads();
+    }
+}
+
+// pv2[j] = core code of ocol[j], or -1.
+__global__ void k_core_codes(const int32_t *ocol, int64_t m, const int32_t *core_of, int32_t *pv2) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        pv2[j] = core_of[ocol[j]];
+}
+
+// ------------------------------------------------------------------ core visits
+
+// Persistent kernel, one 1024-thread block per SM: block visits of core
+// centres.  Per chunk of N+(c): set the members' bits and their words' first
+// positions, run the batches, flush the counters and clear the bits again.
+__global__ void __launch_bounds__(C_THREADS, 1)
+k_support_core(const int64_t *off, const int32_t *col, const uint32_t *flags, const int64_t *ooff,
+               const int32_t *ocol, const int32_t *pv2, const int32_t *core_of, uint32_t *t, const uint64_t *ctasks,
+               unsigned long long *ctr) {
+    extern __shared__ unsigned long long csm[];
+    unsigned long long *bm = csm;                                           // C_WORDS
+    uint16_t *pref = reinterpret_cast<uint16_t *>(bm + C_WORDS);            // C_WORDS
+    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(pref + C_WORDS);         // C_CHUNK
+    __shared__ CoreScratch s_cws[C_WARPS];
+    __shared__ long long s_item;
+    __shared__ int s_next;
+    if (graph_bad(ctr)) return;
+    const unsigned lane = lane_id();
+    CoreScratch &ws = s_cws[threadIdx.x >> 5];
+    for (int i = threadIdx.x; i < C_WORDS; i += C_THREADS) bm[i] = 0ull;
+    for (int i = threadIdx.x; i < C_CHUNK; i += C_THREADS) s_cnt[i] = 0u;
+    __syncthreads();
+    const int64_t ntasks = (int64_t)ctr[C_NCTASK];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(&ctr[C_NEXTC], 1ull);
+        __syncthreads();
+        const int64_t it = s_item;
+        __syncthreads();
+        if (it >= ntasks) break;
+        const uint64_t task = ctasks[it];
+        const int32_t c = (int32_t)(task >> 32);
+        const int64_t vis = (int64_t)(task & VIS_MASK);
+        const int64_t cb = ooff[c];
+        const int64_t du = ooff[c + 1] - cb;
+        const int64_t deg = off[c + 1] - off[c];
+        const int64_t ncand = du + (deg > du ? deg : 0);
+        const int64_t vl = visit_len(du);
+        const int64_t qbeg = vis * vl, qend = min(ncand, qbeg + vl);
+        const bool chunked = du > C_CHUNK;
+        const int32_t cval = core_of[c];
+        for (int64_t c0 = 0; c0 < du; c0 += C_CHUNK) {
+            const int cl = (int)min((int64_t)C_CHUNK, du - c0);
+            for (int i = threadIdx.x; i < cl; i += C_THREADS) {
+                const int32_t w = pv2[cb + c0 + i];
+                if (w >= 0) atomicOr(&bm[w >> 6], 1ull << (w & 63));
+                else flag_status(ctr, ST_BADGRAPH);   // a core centre has only core out-neighbours
+            }
+            if (threadIdx.x == 0) s_next = 0;
+            __syncthreads();
+            for (int i = threadIdx.x; i < cl; i += C_THREADS) {
+                const int32_t w = pv2[cb + c0 + i];
+                if (w >= 0 && !(i > 0 && (pv2[cb + c0 + i - 1] >> 6) == (w >> 6)))   // the word's first member
+                    pref[w >> 6] = (uint16_t)i;
+            }
+            __syncthreads();
+            const CoreSet S{bm, pref, s_cnt};
+            const int32_t lo_id = ocol[cb + c0], hi_id = ocol[cb + c0 + cl - 1];
+            for (;;) {
+                int b = 0;
+                if (lane == 0) b = atomicAdd(&s_next, 32);
+                b = __shfl_sync(FULL, b, 0);
+                if (qbeg + b >= qend) break;
+                process_batch(off, col, flags, ooff, ocol, pv2, t, c, cval, cb, du, qbeg + b, qend, chunked, lo_id,
+                              hi_id, S, s_cnt, false, ws, ctr);
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < cl; i += C_THREADS) {
+                const uint32_t cv = s_cnt[i];
+                if (cv) {
+                    atomicAdd(&t[cb + c0 + i], cv);
+                    s_cnt[i] = 0u;
+                }
+                const int32_t w = pv2[cb + c0 + i];
+                if (w >= 0) bm[w >> 6] = 0ull;
+            }
+            __syncthreads();
+        }
+    }
 }
 
 }  // namespace
@@ -520,9 +748,32 @@ int64_t support_task_capacity(int64_t n, int64_t nnz) {
     return n + (nnz + nnz / 2) / 256 + 64;
 }
 
+cudaError_t launch_core_labels(const int32_t *deg, int64_t n, const int32_t *ocol, int64_t m,
+                               unsigned long long *hist, long long *meta, int64_t *tcnt, int64_t *tbase,
+                               int64_t *bsum, int32_t *core_of, int32_t *pv2, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(hist, 0, 33 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        const int64_t g = ceil_div(n, 256);
+        k_degree_log_hist<<<(unsigned)(g < 4096 ? g : 4096), 256, 0, s>>>(deg, n, hist);
+    }
+    k_core_pick<<<1, 1, 0, s>>>(hist, meta);
+    const int64_t ntiles = ceil_div(n > 0 ? n : 1, (int64_t)TILE);
+    k_core_count<<<(unsigned)ntiles, TILE_THREADS, 0, s>>>(deg, n, meta, tcnt);
+    if ((e = scan_exclusive_i64(tcnt, ntiles, tbase, bsum, s)) != cudaSuccess) return e;
+    k_core_fill<<<(unsigned)ntiles, TILE_THREADS, 0, s>>>(deg, n, meta, tbase, core_of);
+    if (m > 0) {
+        const int64_t g = ceil_div(m, 256);
+        k_core_codes<<<(unsigned)(g < 65536 ? g : 65536), 256, 0, s>>>(ocol, m, core_of, pv2);
+    }
+    count_launches(n > 0 ? 6 : 5);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_support(const int64_t *off, const int32_t *col, const uint32_t *flags, const int64_t *ooff,
                            const int32_t *ocol, int64_t n, int64_t m, uint32_t *t, uint64_t *tasks,
-                           int64_t task_cap, unsigned long long *ctr, int num_sms, cudaStream_t s) {
+                           int64_t task_cap, unsigned long long *ctr, int num_sms, cudaStream_t s,
+                           const int32_t *pv2, const int32_t *core_of, uint64_t *ctasks) {
     if (m > 0) {
         cudaError_t e = cudaMemsetAsync(t, 0, (size_t)m * sizeof(uint32_t), s);
         if (e != cudaSuccess) return e;
@@ -531,13 +782,25 @@ cudaError_t launch_support(const int64_t *off, const int32_t *col, const uint32_
     const int bsmem = B_WORDS * (int)sizeof(int32_t);
     cudaError_t e = cudaFuncSetAttribute(k_support, cudaFuncAttributeMaxDynamicSharedMemorySize, bsmem);
     if (e != cudaSuccess) return e;
+    const bool core = pv2 && core_of && ctasks;
+    if (core) {
+        e = cudaFuncSetAttribute(k_support_core, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_SMEM);
+        if (e != cudaSuccess) return e;
+    }
     k_reset_support_counters<<<1, 1, 0, s>>>(ctr);
     {
         const int64_t g = ceil_div(n, 256);
-        k_make_visits<<<(unsigned)(g < 65536 ? g : 65536), 256, 0, s>>>(off, ooff, n, tasks, task_cap, ctr);
+        k_make_visits<<<(unsigned)(g < 65536 ? g : 65536), 256, 0, s>>>(off, ooff, n, tasks, task_cap,
+                                                                        core ? core_of : nullptr, ctasks, ctr);
+    }
+    int launched = 2;
+    if (core) {
+        k_support_core<<<(unsigned)num_sms, C_THREADS, C_SMEM, s>>>(off, col, flags, ooff, ocol, pv2, core_of, t,
+                                                                    ctasks, ctr);
+        ++launched;
     }
     k_support<<<(unsigned)(num_sms * 2), B_THREADS, bsmem, s>>>(off, col, flags, ooff, ocol, t, tasks, task_cap, ctr);
-    count_launches(3);
+    count_launches(launched + 1);
     return cudaGetLastError();
 }
 

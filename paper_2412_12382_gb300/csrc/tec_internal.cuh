@@ -34,6 +34,8 @@ enum Ctr : int {
     C_NEXT = 5,
     C_NEXTW = 6,
     C_CHANGED = 7,
+    C_NCTASK = 8,       // core block visits
+    C_NEXTC = 9,        // next core block visit
     C_COUNT = 16
 };
 
@@ -98,10 +100,19 @@ cudaError_t launch_orient(const int64_t *off, const int32_t *col, const int32_t 
 // support.cu: t[j] for every oriented edge (zeroed inside).  `flags` are the
 // orientation bits of the symmetric entries; `tasks` holds task_cap entries.
 int64_t support_task_capacity(int64_t n, int64_t nnz);
-cudaError_t launch_support(const int64_t *off, const int32_t *col, const uint32_t *flags,
-                           const int64_t *ooff, const int32_t *ocol, int64_t n, int64_t m,
-                           uint32_t *t, uint64_t *tasks, int64_t task_cap,
-                           unsigned long long *ctr, int num_sms, cudaStream_t s);
+// Core labels for the support kernel: degree >= D vertices numbered in id
+// order (core_of, -1 otherwise; D the smallest power of two with at most 2^20
+// of them, meta = {D, K}) and pv2[j] = core_of[ocol[j]].  hist: 33 entries;
+// tcnt / tbase: ceil(n / TILE) entries each; bsum: scan scratch.
+cudaError_t launch_core_labels(const int32_t *deg, int64_t n, const int32_t *ocol, int64_t m,
+                               unsigned long long *hist, long long *meta, int64_t *tcnt, int64_t *tbase,
+                               int64_t *bsum, int32_t *core_of, int32_t *pv2, cudaStream_t s);
+// Triangle counts; with pv2 / core_of / ctasks (capacity task_cap) block
+// visits of core centres run in the bitmap kernel.
+cudaError_t launch_support(const int64_t *off, const int32_t *col, const uint32_t *flags, const int64_t *ooff,
+                           const int32_t *ocol, int64_t n, int64_t m, uint32_t *t, uint64_t *tasks,
+                           int64_t task_cap, unsigned long long *ctr, int num_sms, cudaStream_t s,
+                           const int32_t *pv2, const int32_t *core_of, uint64_t *ctasks);
 
 // prune.cu
 struct PruneArgs {
@@ -338,6 +349,14 @@ struct tec_graph {
     unsigned long long *msf_k = nullptr;  // live-edge list: edge keys
     int32_t *msf_cnt = nullptr;           // live entries per tile region
     int64_t msf_cap = 0;                  // entries allocated (0: no list, rounds rescan the CSR)
+    // core staging of the support kernel (optional: without it all block visits hash)
+    int32_t *core_of = nullptr;           // n: core code or -1
+    int32_t *pv2 = nullptr;               // m + 4: core codes of ocol
+    uint64_t *ctasks = nullptr;           // task_cap core block visits
+    int64_t *core_tc = nullptr;           // 2 x ceil(n_cap / TILE) + 64: tile counts and bases
+    unsigned long long *core_hist = nullptr;  // 33 degree bins + 2 meta words
+    int core_state = 0;                   // 0 untried, 1 available, -1 unavailable
+    bool core_enabled = true;             // tec_set_core_staging
     unsigned long long *msf_changed = nullptr;  // 64 per-round "a tree grew" flags
     int32_t *fu = nullptr, *fv = nullptr; // n: forest edges bucketed by level
     unsigned long long *bucket = nullptr; // 3k+4 bucket counts / offsets / cursors

@@ -75,6 +75,7 @@ SIGNATURES = {
     "tec_pick_threshold": ([_P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
     "tec_sweep_stats": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "tec_rule_of_thumb": ([_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
+    "tec_set_core_staging": ([_P, ctypes.c_int], ctypes.c_int),
     "tec_components_noalloc": ([_I64, _I64, _P, _P, _P, _P, _PI64, _P], ctypes.c_int),
 }
 
@@ -323,6 +324,10 @@ class Graph:
         check(self._lib.tec_ari(self._h, k, _ptr(labels.contiguous()), _ptr(truth.contiguous()),
                                 _ptr(seg_off) if seg_off is not None else None, nseg, _ptr(out)))
         return out
+
+    def set_core_staging(self, enable: bool):
+        """Exact bitmap staging of high-degree centres in the triangle counts (default on)."""
+        check(self._lib.tec_set_core_staging(self._h, int(bool(enable))))
 
     def sweep_stats(self, measure: int, ps, qs, labels, seg_off=None):
         """Statistics of k nested labelings (k x n CUDA int32, rows at ps[i]/qs[i]):

@@ -60,6 +60,11 @@ def check_all(tec, off, col, thresholds):
         flab, fnc = g.full_pass(measure, p, q)
         assert fnc == nc
         assert np.array_equal(flab.cpu().numpy(), labels)
+    # the other staging of the triangle counts (hashed for every centre) gives the same counts
+    g.set_core_staging(False)
+    gt2, _ = g.edge_support()
+    assert np.array_equal(_u32(gt2), t)
+    g.set_core_staging(True)
     g.free()
 
 
@@ -113,7 +118,7 @@ def test_imbalanced_sbm_theorem1(tec):
 
 def test_complete_graph_chunked_rows(tec):
     # K_9000: every degree ties, so ranks follow ids and vertex 0 has 8999
-    # oriented neighbours, more than one shared-memory chunk (8192).  Closed
+    # oriented neighbours, more than one shared-memory chunk.  Closed
     # form: t = n - 2 on every edge, wedge = 0.
     import torch
     k = 9000
@@ -123,9 +128,11 @@ def test_complete_graph_chunked_rows(tec):
         col[u * (k - 1):(u + 1) * (k - 1)] = np.delete(ids, u)
     off = np.arange(0, k * (k - 1) + 1, k - 1, dtype=np.int64)
     g = _gpu_graph(tec, off, col, validate=False)
-    t, w = g.edge_support()
-    assert int(t.min()) == k - 2 and int(t.max()) == k - 2
-    assert int(w.min()) == 0 and int(w.max()) == 0
+    for core in (True, False):       # bitmap chunks of 8192 ids, hashed chunks of 4096
+        g.set_core_staging(core)
+        t, w = g.edge_support()
+        assert int(t.min()) == k - 2 and int(t.max()) == k - 2
+        assert int(w.min()) == 0 and int(w.max()) == 0
     lab, nc = g.full_pass(tec.TECTONIC, k - 2, 2 * (k - 1))       # exactly the common weight: keep all
     assert nc == 1 and int(lab.max()) == 0
     lab, nc = g.full_pass(tec.TECTONIC, k - 2 + 1, 2 * (k - 1))   # just above: drop all

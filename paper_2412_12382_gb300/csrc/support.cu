@@ -47,6 +47,10 @@ constexpr int64_t VISIT_PROBES_W = 1 << 20;     // target probes per warp visit
 // hold many batches per warp for that tail to stay small.
 constexpr int64_t VISIT_PROBES_B = 1 << 25;
 constexpr int W_GRAB = 16;                      // warp visits taken per counter bump
+// Candidates per batch of a block visit.  A visit ends at a block barrier, and
+// one batch of long rows can hold many times the average batch's probes, so
+// batches smaller than a warp keep the barrier tail short.
+constexpr int B_BATCH = 8;
 constexpr uint64_t VIS_MASK = (1ull << 32) - 1;
 
 __device__ __forceinline__ bool out_bit(const uint32_t *flags, int64_t e) {
@@ -344,7 +348,7 @@ struct CoreSet {
     __device__ __forceinline__ void finish(uint32_t *, CoreScratch &, int &) const {}
 };
 
-// One warp processes candidates q0 .. min(q0 + 32, qend) - 1 of centre c
+// One warp processes candidates q0 .. min(q0 + 32, qend) - 1 of centre c (a batch)
 // against the staged chunk S.  Rows longer than SHORT_ROW are read one at a
 // time by the whole warp; the shorter ones are laid end to end over the lanes
 // (each lane finds the row of its id by a 5-step shuffle search over the
@@ -543,10 +547,11 @@ k_support(const int64_t *off, const int32_t *col, const uint32_t *flags, const i
             __syncthreads();
             for (;;) {
                 int b = 0;
-                if (lane == 0) b = atomicAdd(&s_next, 32);
+                if (lane == 0) b = atomicAdd(&s_next, B_BATCH);
                 b = __shfl_sync(FULL, b, 0);
                 if (qbeg + b >= qend) break;
-                process_batch(off, col, flags, ooff, ocol, ocol, t, c, c, cb, du, qbeg + b, qend, chunked, S.a[0],
+                process_batch(off, col, flags, ooff, ocol, ocol, t, c, c, cb, du, qbeg + b,
+                              min(qend, qbeg + b + B_BATCH), chunked, S.a[0],
                               S.a[S.cl - 1], FilterSet{S}, S.cnt, false, ws, ctr);
             }
             __syncthreads();
@@ -720,11 +725,11 @@ k_support_core(const int64_t *off, const int32_t *col, const uint32_t *flags, co
             const int32_t lo_id = ocol[cb + c0], hi_id = ocol[cb + c0 + cl - 1];
             for (;;) {
                 int b = 0;
-                if (lane == 0) b = atomicAdd(&s_next, 32);
+                if (lane == 0) b = atomicAdd(&s_next, B_BATCH);
                 b = __shfl_sync(FULL, b, 0);
                 if (qbeg + b >= qend) break;
-                process_batch(off, col, flags, ooff, ocol, pv2, t, c, cval, cb, du, qbeg + b, qend, chunked, lo_id,
-                              hi_id, S, s_cnt, false, ws, ctr);
+                process_batch(off, col, flags, ooff, ocol, pv2, t, c, cval, cb, du, qbeg + b,
+                              min(qend, qbeg + b + B_BATCH), chunked, lo_id, hi_id, S, s_cnt, false, ws, ctr);
             }
             __syncthreads();
             for (int i = threadIdx.x; i < cl; i += C_THREADS) {

@@ -145,14 +145,17 @@ int64_t orc_components(int64_t n, int64_t m, const int32_t *eu, const int32_t *e
  *   measure 0, Tectonic (Table 1): sim = t / (deg u + deg v),
  *       keep iff t*q >= p*(deg u + deg v);
  *   measure 1, TW (Eq. 1): sim = t - wedge with
- *       wedge = |N(u) u N(v)| - t - 2 (Sec. I), keep iff (t - wedge)*q >= p.
+ *       wedge = |N(u) u N(v)| - t - 2 (Sec. I), keep iff (t - wedge)*q >= p;
+ *   measure 2, Jaccard (Table 1): sim = t / |N(u) u N(v)|, the union
+ *       being deg u + deg v - t > 0, keep iff t*q >= p*|N(u) u N(v)|;
+ *   measure 3, K3 (Table 1): sim = t, keep iff t*q >= p.
  * Returns the number of kept edges, or -1 on a bad argument. */
 int64_t orc_prune(int measure, const int64_t *off, int64_t m,
                   const int32_t *eu, const int32_t *ev,
                   const uint32_t *inter, const uint32_t *uni,
                   int64_t p, int64_t q, uint8_t *keep)
 {
-    if (q <= 0 || (measure != 0 && measure != 1)) return -1;
+    if (q <= 0 || measure < 0 || measure > 3) return -1;
     int64_t kept = 0;
     for (int64_t e = 0; e < m; ++e) {
         __int128 t = inter[e];
@@ -161,9 +164,13 @@ int64_t orc_prune(int measure, const int64_t *off, int64_t m,
             __int128 du = off[eu[e] + 1] - off[eu[e]];
             __int128 dv = off[ev[e] + 1] - off[ev[e]];
             k = t * q >= (__int128)p * (du + dv);
-        } else {
+        } else if (measure == 1) {
             __int128 wedge = (__int128)uni[e] - t - 2;
             k = (t - wedge) * q >= (__int128)p;
+        } else if (measure == 2) {
+            k = t * q >= (__int128)p * (__int128)uni[e];
+        } else {
+            k = t * q >= (__int128)p;
         }
         keep[e] = (uint8_t)k;
         kept += k;

@@ -28,6 +28,8 @@ from .build import library_path, build_oracle
 
 TECTONIC = 0
 TW = 1
+JACCARD = 2
+K3 = 3
 
 _lib = None
 
@@ -121,6 +123,16 @@ def tectonic_weights(off, eu, ev, t):
     d = degrees(off)
     s = (d[np.asarray(eu)] + d[np.asarray(ev)]).astype(np.float64)
     return np.asarray(t, dtype=np.float64) / s
+
+
+def jaccard_weights(t, uni):
+    """Jaccard similarity |N(u) n N(v)| / |N(u) u N(v)| (Table 1, Sec. II), one IEEE binary64 division."""
+    return np.asarray(t, dtype=np.float64) / np.asarray(uni, dtype=np.float64)
+
+
+def k3_scores(t):
+    """K3 similarity: the triangle count t(u,v) itself (Table 1), exact."""
+    return np.asarray(t, dtype=np.int64)
 
 
 def tw_scores(t, wedge):

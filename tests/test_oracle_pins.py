@@ -240,6 +240,39 @@ def test_prop1_jaccard_is_reparametrised_tectonic():
             assert (keep == jac_keep).all()
 
 
+def test_jaccard_and_k3_prune_by_definition():
+    # Jaccard from the neighbourhood sets (Sec. II) and K3 = t (Table 1), against Fraction
+    for off, col in _rand_graphs(6, seed=41):
+        eu, ev = O.edge_list(off, col)
+        if len(eu) == 0:
+            continue
+        t, uni = O.edge_counts(off, col, eu, ev)
+        nb = [set(col[off[v]:off[v + 1]].tolist()) for v in range(len(off) - 1)]
+        jac = [Fraction(len(nb[a] & nb[b]), len(nb[a] | nb[b])) for a, b in zip(eu, ev)]
+        w = O.jaccard_weights(t, uni)
+        assert all(w[e] == float(jac[e]) for e in range(len(eu)))
+        for p, q in ((0, 1), (1, 10), (1, 3), (2, 3), (1, 1), (-1, 2)):
+            keep, kept = O.prune(O.JACCARD, off, eu, ev, t, uni, p, q)
+            assert list(keep) == [1 if j >= Fraction(p, q) else 0 for j in jac] and kept == int(keep.sum())
+        for p, q in ((0, 1), (1, 1), (3, 2), (2, 1), (7, 3), (100, 1)):
+            keep, _ = O.prune(O.K3, off, eu, ev, t, uni, p, q)
+            assert list(keep) == [1 if Fraction(int(x)) >= Fraction(p, q) else 0 for x in t]
+        assert np.array_equal(O.k3_scores(t), t.astype(np.int64))
+
+
+def test_prop1_as_two_oracle_prunes():
+    # Proposition 1 exactly: Jaccard at p/q keeps what Tectonic at p/(p+q) keeps (p >= 0)
+    for off, col in _rand_graphs(6, seed=43):
+        eu, ev = O.edge_list(off, col)
+        if len(eu) == 0:
+            continue
+        t, uni = O.edge_counts(off, col, eu, ev)
+        for p, q in ((0, 1), (1, 10), (1, 3), (7, 9), (1, 1), (5, 2)):
+            kj, _ = O.prune(O.JACCARD, off, eu, ev, t, uni, p, q)
+            kt, _ = O.prune(O.TECTONIC, off, eu, ev, t, uni, p, p + q)
+            assert np.array_equal(kj, kt)
+
+
 def test_prune_rejects_nonpositive_q():
     off, col = small.complete(4)
     eu, ev = O.edge_list(off, col)

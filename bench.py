@@ -43,8 +43,9 @@ WORKLOADS = {
 # DRAM bytes per launch of the triangle-count stage from an ncu capture, per
 # unit of algorithmic bytes, valid only for the support.cu it was taken on
 # (see profiles/).  None until a capture exists for the current source.
-TRAFFIC_CAPTURE = {"support_sha": "f077fe23de50fc0b", "dram_per_alg_byte": 84.066287 / 49.162954,
-                   "source": "ncu DRAM bytes of k_support at R-MAT scale 22, scaled by algorithmic bytes"}
+TRAFFIC_CAPTURE = {"support_sha": "f81bcfd5a07a1ecf", "dram_per_alg_byte": 83.728 / 49.162954,
+                   "source": "ncu DRAM bytes of the triangle-count stage's kernels at R-MAT scale 22, "
+                             "scaled by algorithmic bytes"}
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"

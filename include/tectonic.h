@@ -59,7 +59,9 @@ typedef enum tec_status {
 /* Similarity functions of Table 1. */
 typedef enum tec_measure {
     TEC_TECTONIC = 0,   /* t(u,v) / (deg u + deg v) */
-    TEC_TW = 1          /* t(u,v) - wedge(u,v) = 3 t(u,v) + 2 - deg u - deg v (Eq. 1) */
+    TEC_TW = 1,         /* t(u,v) - wedge(u,v) = 3 t(u,v) + 2 - deg u - deg v (Eq. 1) */
+    TEC_JACCARD = 2,    /* t(u,v) / |N(u) u N(v)| = t / (deg u + deg v - t) (Sec. II, Proposition 1) */
+    TEC_K3 = 3          /* t(u,v), the edge's triangle count */
 } tec_measure;
 
 /* tec_graph_load flags */
@@ -130,7 +132,9 @@ tec_status tec_edge_support(tec_graph *g, uint32_t *t_out, uint32_t *wedge_out);
 
 /* Similarity of every edge as float64 in canonical order (device):
  * TEC_TECTONIC: t / (deg u + deg v), one correctly rounded IEEE division;
- * TEC_TW: t - wedge, an integer, exactly representable. */
+ * TEC_TW: t - wedge, an integer, exactly representable;
+ * TEC_JACCARD: t / (deg u + deg v - t), one correctly rounded IEEE division;
+ * TEC_K3: t, exactly representable. */
 tec_status tec_edge_weights(tec_graph *g, tec_measure measure, double *w_out);
 
 /* Algorithm 1, first step: keeps edge e iff sim(e) >= p/q, i.e. removes

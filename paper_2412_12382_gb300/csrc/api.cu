@@ -158,7 +158,7 @@ tec_status ensure_uoff(tec_graph *g) {
 }
 
 tec_status check_threshold(int measure, int64_t p, int64_t q) {
-    if (measure != TEC_TECTONIC && measure != TEC_TW) return set_error(TEC_EINVAL, "unknown measure %d", measure);
+    if (measure < TEC_TECTONIC || measure > TEC_K3) return set_error(TEC_EINVAL, "unknown measure %d", measure);
     if (q <= 0) return set_error(TEC_EINVAL, "threshold denominator q must be positive (got %lld)", (long long)q);
     if (q >= THRESH_LIMIT || p >= THRESH_LIMIT || p <= -THRESH_LIMIT)
         return set_error(TEC_EOVERFLOW, "|p| and q must be below 2^62");
@@ -496,7 +496,7 @@ tec_status tec_edge_support(tec_graph *g, uint32_t *t_out, uint32_t *wedge_out) 
 tec_status tec_edge_weights(tec_graph *g, tec_measure measure, double *w_out) {
     clear_error();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
-    if (measure != TEC_TECTONIC && measure != TEC_TW) return set_error(TEC_EINVAL, "unknown measure %d", (int)measure);
+    if (measure < TEC_TECTONIC || measure > TEC_K3) return set_error(TEC_EINVAL, "unknown measure %d", (int)measure);
     if (!w_out && g->m > 0) return set_error(TEC_EINVAL, "w_out is NULL");
     DeviceGuard dg(g->device);
     TEC_TRY(ensure_support(g));
@@ -746,7 +746,7 @@ tec_status tec_prune_components_batch(tec_graph *g, tec_measure measure, const i
                                       const int64_t *seg_off, int nseg, int32_t *labels_out, int64_t *ncomp_out) {
     clear_error();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
-    if (measure != TEC_TECTONIC && measure != TEC_TW) return set_error(TEC_EINVAL, "unknown measure %d", (int)measure);
+    if (measure < TEC_TECTONIC || measure > TEC_K3) return set_error(TEC_EINVAL, "unknown measure %d", (int)measure);
     if (!p || !q || !seg_off || nseg < 1) return set_error(TEC_EINVAL, "thresholds and segment table are required");
     if (!labels_out && g->n > 0) return set_error(TEC_EINVAL, "labels_out is NULL");
     DeviceGuard dg(g->device);

@@ -155,6 +155,8 @@ k_export(const int64_t *off, const int32_t *col, const int32_t *deg, const int64
         if (wedge_out) wedge_out[e] = (uint32_t)(s - 2 * (int64_t)tt - 2);
         if (w_out) {
             if (w_measure == TEC_TECTONIC) w_out[e] = __ddiv_rn((double)tt, (double)s);
+            else if (w_measure == TEC_JACCARD) w_out[e] = __ddiv_rn((double)tt, (double)(s - (int64_t)tt));
+            else if (w_measure == TEC_K3) w_out[e] = (double)tt;
             else w_out[e] = (double)(3 * (int64_t)tt + 2 - s);
         }
         if (keep_out) keep_out[e] = (uint8_t)((keep[pos >> 5] >> (pos & 31)) & 1u);

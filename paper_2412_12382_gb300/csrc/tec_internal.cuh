@@ -284,13 +284,24 @@ __device__ __forceinline__ bool rank_less(int32_t du, int64_t u, int32_t dv, int
 
 // Algorithm 1's survival test sim(e) >= p/q in exact integers, given
 // t = t(u,v) and s = deg u + deg v (q > 0):
-//   Tectonic (Table 1): t*q >= p*s;   TW (Eq. 1): (3t + 2 - s)*q >= p.
+//   Tectonic (Table 1): t*q >= p*s;   TW (Eq. 1): (3t + 2 - s)*q >= p;
+//   Jaccard (Table 1): t*q >= p*(s - t), s - t = |N(u) u N(v)| > 0;
+//   K3 (Table 1): t*q >= p.
 // All products fit int64 when |p|, q < 2^28; WIDE uses 128-bit products.
 template <bool WIDE>
 __device__ __forceinline__ bool keep_edge(int measure, uint32_t tt, int64_t s, int64_t p, int64_t q) {
     if (measure == TEC_TECTONIC) {
         if (WIDE) return (__int128)tt * q >= (__int128)p * s;
         return (int64_t)tt * q >= p * s;
+    }
+    if (measure == TEC_JACCARD) {
+        const int64_t uni = s - (int64_t)tt;
+        if (WIDE) return (__int128)tt * q >= (__int128)p * uni;
+        return (int64_t)tt * q >= p * uni;
+    }
+    if (measure == TEC_K3) {
+        if (WIDE) return (__int128)tt * q >= (__int128)p;
+        return (int64_t)tt * q >= p;
     }
     const int64_t tw = 3 * (int64_t)tt + 2 - s;
     if (WIDE) return (__int128)tw * q >= (__int128)p;

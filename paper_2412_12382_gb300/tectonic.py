@@ -16,6 +16,8 @@ from . import build as _build
 
 TECTONIC = 0
 TW = 1
+JACCARD = 2
+K3 = 3
 HOST_PTR = 0x1
 VALIDATE = 0x2
 

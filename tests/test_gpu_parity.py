@@ -48,6 +48,9 @@ def check_all(tec, off, col, thresholds):
     assert np.array_equal(w_tec.view(np.uint64), O.tectonic_weights(off, eu, ev, t).view(np.uint64))
     w_tw = g.edge_weights(tec.TW).cpu().numpy()
     assert np.array_equal(w_tw, O.tw_scores(t, wedge).astype(np.float64))
+    w_jac = g.edge_weights(tec.JACCARD).cpu().numpy()
+    assert np.array_equal(w_jac.view(np.uint64), O.jaccard_weights(t, uni).view(np.uint64))
+    assert np.array_equal(g.edge_weights(tec.K3).cpu().numpy(), O.k3_scores(t).astype(np.float64))
     for measure, p, q in thresholds:
         keep, kept = O.prune(measure, off, eu, ev, t, uni, p, q)
         labels, nc = O.components(n, eu, ev, keep)
@@ -68,7 +71,8 @@ def check_all(tec, off, col, thresholds):
     g.free()
 
 
-STD = [(O.TECTONIC, 1, 10), (O.TECTONIC, 3, 50), (O.TW, -30, 1), (O.TW, 0, 1), (O.TW, 3, 50)]
+STD = [(O.TECTONIC, 1, 10), (O.TECTONIC, 3, 50), (O.TW, -30, 1), (O.TW, 0, 1), (O.TW, 3, 50),
+       (O.JACCARD, 1, 5), (O.JACCARD, 1, 2), (O.K3, 3, 1), (O.K3, 7, 2)]
 
 
 @pytest.mark.parametrize("name,graph", [
@@ -252,3 +256,19 @@ def test_dcsbm_gpu_batch_matches_host(cuda_device):
     assert np.array_equal(goff.cpu().numpy(), off)
     assert np.array_equal(gcol.cpu().numpy(), col)
     assert np.array_equal(gtruth.cpu().numpy(), np.concatenate([h[2] for h in host]))
+
+
+def test_jaccard_sweep_and_prop1_on_device(tec):
+    """Jaccard at p/q and Tectonic at p/(p+q) give the same components on the
+    device (Proposition 1), and a Jaccard sweep equals the oracle's passes."""
+    import torch
+    off, col, _ = planted_partition(4, 500, 0.05, 0.002, seed=1)
+    g = _gpu_graph(tec, off, col)
+    ps, qs = [1, 1, 1, 2, 3], [20, 10, 5, 5, 5]
+    lab, nc = g.sweep(tec.JACCARD, ps, qs)
+    ol, onc = O.sweep(off, col, O.JACCARD, ps, qs)
+    assert np.array_equal(lab.cpu().numpy(), ol) and np.array_equal(nc, onc)
+    for i, (p, q) in enumerate(zip(ps, qs)):
+        tl, _ = g.full_pass(tec.TECTONIC, p, p + q)
+        assert torch.equal(tl, lab[i])
+    g.free()

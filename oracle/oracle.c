@@ -98,6 +98,57 @@ void orc_edge_counts(const int64_t *off, const int32_t *col, int64_t m,
     }
 }
 
+/* K4 participation (Table 1, kappa = 4): for each edge e = (u, v) the number
+ * of 4-cliques containing it, i.e. the number of edges {c, d} with both ends
+ * in the common neighbourhood C = N(u) n N(v).  C is built by merging the two
+ * sorted rows; each c in C is merged with C once more, counting the d > c of
+ * N(c) that lie in C. */
+void orc_edge_k4(const int64_t *off, const int32_t *col, int64_t m, const int32_t *eu, const int32_t *ev,
+                 uint64_t *k4, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        int64_t cap = 64;
+        int32_t *cs = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+        for (int64_t e = 0; e < m; ++e) {
+            int64_t i = off[eu[e]], iend = off[eu[e] + 1];
+            int64_t j = off[ev[e]], jend = off[ev[e] + 1];
+            int64_t nc = 0;
+            while (i < iend && j < jend) {
+                if (col[i] < col[j]) ++i;
+                else if (col[i] > col[j]) ++j;
+                else {
+                    if (nc == cap) {
+                        cap *= 2;
+                        cs = (int32_t *)realloc(cs, (size_t)cap * sizeof(int32_t));
+                    }
+                    cs[nc++] = col[i];
+                    ++i;
+                    ++j;
+                }
+            }
+            uint64_t count = 0;
+            for (int64_t a = 0; a < nc; ++a) {
+                const int32_t c = cs[a];
+                int64_t x = off[c], xend = off[c + 1], y = a + 1;
+                while (x < xend && y < nc) {             /* N(c) merged with the d > c of C */
+                    if (col[x] < cs[y]) ++x;
+                    else if (col[x] > cs[y]) ++y;
+                    else { ++count; ++x; ++y; }
+                }
+            }
+            k4[e] = count;
+        }
+        free(cs);
+    }
+}
+
 /* Connected components of (V, {e : keep[e]}) over the canonical edge list
  * (Algorithm 1, second step).  Breadth-first search started from every
  * unvisited vertex in increasing id order, so the start vertex is the smallest

@@ -30,6 +30,7 @@ TECTONIC = 0
 TW = 1
 JACCARD = 2
 K3 = 3
+K4 = 4
 
 _lib = None
 
@@ -54,6 +55,8 @@ def _load():
     lib.orc_components.restype = i64
     lib.orc_prune.argtypes = [ctypes.c_int, P, i64, P, P, P, P, i64, i64, P]
     lib.orc_prune.restype = i64
+    lib.orc_edge_k4.argtypes = [P, P, i64, P, P, P, ctypes.c_int]
+    lib.orc_edge_k4.restype = None
     lib.orc_num_threads_available.argtypes = []
     lib.orc_num_threads_available.restype = ctypes.c_int
     _lib = lib
@@ -135,15 +138,34 @@ def k3_scores(t):
     return np.asarray(t, dtype=np.int64)
 
 
+def edge_k4(off, col, eu=None, ev=None, nthreads: int = 1):
+    """K4 participation (Table 1, kappa = 4): 4-cliques containing each edge, in
+    canonical edge order (uint64)."""
+    off, col = _csr(off, col)
+    if eu is None:
+        eu, ev = edge_list(off, col)
+    eu = np.ascontiguousarray(eu, dtype=np.int32)
+    ev = np.ascontiguousarray(ev, dtype=np.int32)
+    k4 = np.empty(eu.size, dtype=np.uint64)
+    _load().orc_edge_k4(_p(off), _p(col), eu.size, _p(eu), _p(ev), _p(k4), int(nthreads))
+    return k4
+
+
 def tw_scores(t, wedge):
     """TW(e) = t(e) - wedge(e) (Eq. 1), exact int64."""
     return np.asarray(t, dtype=np.int64) - np.asarray(wedge, dtype=np.int64)
 
 
-def prune(measure: int, off, eu, ev, t, uni, p: int, q: int):
-    """keep[e] = 1 iff sim(e) >= p/q (Algorithm 1 removes exactly the edges with sim < delta)."""
+def prune(measure: int, off, eu, ev, t, uni, p: int, q: int, k4=None):
+    """keep[e] = 1 iff sim(e) >= p/q (Algorithm 1 removes exactly the edges with sim < delta).
+    For K4 the 4-clique counts k4 (edge_k4) are the similarity: keep iff k4*q >= p."""
     if q <= 0:
         raise ValueError("q must be positive")
+    if measure == K4:
+        if k4 is None:
+            raise ValueError("K4 needs the 4-clique counts")
+        keep = np.array([1 if int(x) * q >= p else 0 for x in k4], dtype=np.uint8)
+        return keep, int(keep.sum())
     if not (-(1 << 63) <= p < (1 << 63) and q < (1 << 63)):
         raise ValueError("p and q must fit in int64")
     off = np.ascontiguousarray(off, dtype=np.int64)
@@ -189,7 +211,8 @@ def full_pass(off, col, measure: int, p: int, q: int, nthreads: int = 1) -> Pass
     n = len(off) - 1
     eu, ev = edge_list(off, col)
     t, uni = edge_counts(off, col, eu, ev, nthreads)
-    keep, kept = prune(measure, off, eu, ev, t, uni, p, q)
+    k4 = edge_k4(off, col, eu, ev, nthreads) if measure == K4 else None
+    keep, kept = prune(measure, off, eu, ev, t, uni, p, q, k4)
     labels, nc = components(n, eu, ev, keep)
     return PassResult(eu, ev, t, wedges(t, uni), keep, kept, labels, nc)
 
@@ -200,10 +223,11 @@ def sweep(off, col, measure: int, ps, qs, nthreads: int = 1):
     n = len(off) - 1
     eu, ev = edge_list(off, col)
     t, uni = edge_counts(off, col, eu, ev, nthreads)
+    k4 = edge_k4(off, col, eu, ev, nthreads) if measure == K4 else None
     labels = np.empty((len(ps), n), dtype=np.int32)
     ncomp = np.empty(len(ps), dtype=np.int64)
     for i, (p, q) in enumerate(zip(ps, qs)):
-        keep, _ = prune(measure, off, eu, ev, t, uni, p, q)
+        keep, _ = prune(measure, off, eu, ev, t, uni, p, q, k4)
         labels[i], ncomp[i] = components(n, eu, ev, keep)
     return labels, ncomp
 
@@ -325,9 +349,10 @@ def sweep_stats(off, col, measure: int, ps, qs, labels, nthreads: int = 1):
     t, uni = edge_counts(off, col, eu, ev, nthreads)
     deg = degrees(off)
     m = len(eu)
+    k4 = edge_k4(off, col, eu, ev, nthreads) if measure == K4 else None
     out = []
     for i, (p, q) in enumerate(zip(ps, qs)):
-        _, kept = prune(measure, off, eu, ev, t, uni, p, q)
+        _, kept = prune(measure, off, eu, ev, t, uni, p, q, k4)
         lab = np.asarray(labels[i], dtype=np.int64)
         _, li = np.unique(lab, return_inverse=True)
         size = np.bincount(li)

@@ -450,3 +450,33 @@ def test_upper_pairs_matches_edge_list():
     eu, ev = O.edge_list(off, col)
     u, v = upper_pairs(off, col)
     assert (eu == u).all() and (ev == v).all()
+
+
+def test_k4_participation_closed_forms_and_brute_force():
+    from itertools import combinations
+    # K_n: every edge lies in C(n-2, 2) 4-cliques; a triangle-free graph has none
+    for k in (4, 5, 9):
+        off, col = small.complete(k)
+        assert set(O.edge_k4(off, col).tolist()) == {(k - 2) * (k - 3) // 2}
+    off, col = small.cycle(8)
+    assert not O.edge_k4(off, col).any()
+    off, col = small.two_cliques_bridge(5, 6)
+    eu, ev = O.edge_list(off, col)
+    k4 = O.edge_k4(off, col)
+    assert k4[(eu == 0) & (ev == 1)][0] == 3 and k4[(eu == 5) & (ev == 6)][0] == 6
+    # brute force over 4-subsets; sum of K4(e) = 6 * #4-cliques
+    for off, col in _rand_graphs(5, seed=47):
+        n = len(off) - 1
+        adj = [set(col[off[v]:off[v + 1]].tolist()) for v in range(n)]
+        eu, ev = O.edge_list(off, col)
+        k4 = O.edge_k4(off, col)
+        cliques = [c for c in combinations(range(n), 4)
+                   if all(b in adj[a] for a, b in combinations(c, 2))]
+        ref = {(a, b): 0 for a, b in zip(eu.tolist(), ev.tolist())}
+        for c in cliques:
+            for a, b in combinations(c, 2):
+                ref[(a, b)] += 1
+        assert [int(x) for x in k4] == [ref[(a, b)] for a, b in zip(eu.tolist(), ev.tolist())]
+        assert int(k4.sum()) == 6 * len(cliques)
+        keep, kept = O.prune(O.K4, off, eu, ev, None, None, 3, 2, k4)
+        assert list(keep) == [1 if 2 * int(x) >= 3 else 0 for x in k4]

@@ -61,7 +61,9 @@ typedef enum tec_measure {
     TEC_TECTONIC = 0,   /* t(u,v) / (deg u + deg v) */
     TEC_TW = 1,         /* t(u,v) - wedge(u,v) = 3 t(u,v) + 2 - deg u - deg v (Eq. 1) */
     TEC_JACCARD = 2,    /* t(u,v) / |N(u) u N(v)| = t / (deg u + deg v - t) (Sec. II, Proposition 1) */
-    TEC_K3 = 3          /* t(u,v), the edge's triangle count */
+    TEC_K3 = 3,         /* t(u,v), the edge's triangle count */
+    TEC_K4 = 4          /* K4(u,v), the 4-cliques containing the edge (saturating at 2^32 - 1;
+                           thresholds above 2^32 - 1 are TEC_EOVERFLOW) */
 } tec_measure;
 
 /* tec_graph_load flags */
@@ -130,11 +132,19 @@ tec_status tec_edge_list(tec_graph *g, int32_t *u_out, int32_t *v_out);
  * into wedge_out[m] (Sec. I), both uint32 in canonical order (device). */
 tec_status tec_edge_support(tec_graph *g, uint32_t *t_out, uint32_t *wedge_out);
 
+/* K4 participation (Table 1, kappa = 4): for every edge, the number of
+ * 4-cliques containing it, i.e. the edges {c, d} inside the common
+ * neighbourhood N(u) n N(v).  k4_out: device, m uint32 in canonical order,
+ * saturating at 2^32 - 1.  Runs tec_support if needed; the counts are kept for
+ * TEC_K4 pruning until the triangle counts are recomputed. */
+tec_status tec_edge_k4(tec_graph *g, uint32_t *k4_out);
+
 /* Similarity of every edge as float64 in canonical order (device):
  * TEC_TECTONIC: t / (deg u + deg v), one correctly rounded IEEE division;
  * TEC_TW: t - wedge, an integer, exactly representable;
  * TEC_JACCARD: t / (deg u + deg v - t), one correctly rounded IEEE division;
- * TEC_K3: t, exactly representable. */
+ * TEC_K3: t, exactly representable;
+ * TEC_K4: the K4 participation count (tec_edge_k4), exactly representable. */
 tec_status tec_edge_weights(tec_graph *g, tec_measure measure, double *w_out);
 
 /* Algorithm 1, first step: keeps edge e iff sim(e) >= p/q, i.e. removes

@@ -66,7 +66,7 @@ void free_graph_memory(tec_graph *g) {
                     g->flags, g->tile_cnt, g->tile_base, g->bsum, g->uoff, g->ucnt, g->labels, g->lvl, g->best,
                     g->fu, g->fv, g->bucket, g->thr, g->sw_ncomp, g->seg_hist, g->ari_sums,
                     g->ari_size, g->ari_keys, g->ari_cnt, g->msf_u, g->msf_v, g->msf_k, g->msf_cnt, g->msf_changed,
-                    g->core_of, g->pv2, g->ctasks, g->core_tc, g->core_hist,
+                    g->core_of, g->pv2, g->ctasks, g->core_tc, g->core_hist, g->k4, g->k4_next,
                     g->st_hist, g->st_sums, g->st_cnt_n, g->st_cnt_v, g->ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -142,8 +142,36 @@ tec_status ensure_support(tec_graph *g) {
     TEC_CUDA(launch_support(g->off, g->col, g->flags, g->ooff, g->ocol, g->n, g->m, g->t, g->tasks, g->task_cap,
                             g->ctr, g->num_sms, g->stream, core ? g->pv2 : nullptr, core ? g->core_of : nullptr,
                             core ? g->ctasks : nullptr));
+    ++g->support_epoch;
     g->supported = true;
     g->pruned = g->hooked = false;
+    return TEC_OK;
+}
+
+// K4 participation of the current triangle counts.
+tec_status ensure_k4(tec_graph *g) {
+    TEC_TRY(ensure_support(g));
+    if (g->k4 && g->k4_epoch == g->support_epoch) return TEC_OK;
+    if (!g->k4) TEC_TRY(dalloc(&g->k4, std::max<int64_t>(g->m_cap, 1), "K4 counts"));
+    if (!g->k4_next) TEC_TRY(dalloc(&g->k4_next, 1, "K4 work counter"));
+    TEC_CUDA(launch_k4(g->off, g->col, g->ooff, g->ocol, g->t, g->n, g->m, g->k4_next, g->k4, g->ctr, g->num_sms,
+                       g->stream));
+    g->k4_epoch = g->support_epoch;
+    return TEC_OK;
+}
+
+// The per-edge counts a measure compares and the comparison it uses: K4 is the
+// K3 test on the K4 counts; every other measure works on the triangle counts.
+tec_status measure_counts(tec_graph *g, int measure, const uint32_t **counts, int *cmp) {
+    if (measure == TEC_K4) {
+        TEC_TRY(ensure_k4(g));
+        *counts = g->k4;
+        *cmp = TEC_K3;
+    } else {
+        TEC_TRY(ensure_support(g));
+        *counts = g->t;
+        *cmp = measure;
+    }
     return TEC_OK;
 }
 
@@ -158,10 +186,13 @@ tec_status ensure_uoff(tec_graph *g) {
 }
 
 tec_status check_threshold(int measure, int64_t p, int64_t q) {
-    if (measure < TEC_TECTONIC || measure > TEC_K3) return set_error(TEC_EINVAL, "unknown measure %d", measure);
+    if (measure < TEC_TECTONIC || measure > TEC_K4) return set_error(TEC_EINVAL, "unknown measure %d", measure);
     if (q <= 0) return set_error(TEC_EINVAL, "threshold denominator q must be positive (got %lld)", (long long)q);
     if (q >= THRESH_LIMIT || p >= THRESH_LIMIT || p <= -THRESH_LIMIT)
         return set_error(TEC_EOVERFLOW, "|p| and q must be below 2^62");
+    // K4 counts saturate at 2^32 - 1: comparisons stay exact for thresholds up to that
+    if (measure == TEC_K4 && (__int128)p > (__int128)0xFFFFFFFFll * q)
+        return set_error(TEC_EOVERFLOW, "K4 thresholds must not exceed 2^32 - 1");
     return TEC_OK;
 }
 
@@ -176,12 +207,15 @@ tec_status run_full_pass(tec_graph *g, int measure, int64_t p, int64_t q, int32_
     TEC_TRY(ensure_oriented(g));
     TEC_TRY(stage_mark(g, 1));
     TEC_TRY(ensure_support(g));
+    const uint32_t *cts = nullptr;
+    int cmp = measure;
+    TEC_TRY(measure_counts(g, measure, &cts, &cmp));
     TEC_TRY(stage_mark(g, 2));
     TEC_TRY(reset_counter(g, C_KEPT));
     TEC_TRY(reset_counter(g, C_NCOMP));
     TEC_CUDA(launch_cc_init(g->parent, g->n, g->stream));
-    PruneArgs a{measure, p, q, true};
-    TEC_CUDA(launch_prune(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, a, g->keep, g->parent, g->ctr, g->stream));
+    PruneArgs a{cmp, p, q, true};
+    TEC_CUDA(launch_prune(g->ooff, g->ocol, g->deg, cts, g->n, g->m, a, g->keep, g->parent, g->ctr, g->stream));
     g->pruned = g->hooked = true;
     g->last_measure = measure;
     g->last_p = p;
@@ -493,16 +527,30 @@ tec_status tec_edge_support(tec_graph *g, uint32_t *t_out, uint32_t *wedge_out) 
     return TEC_OK;
 }
 
+tec_status tec_edge_k4(tec_graph *g, uint32_t *k4_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (!k4_out && g->m > 0) return set_error(TEC_EINVAL, "k4_out is NULL");
+    DeviceGuard dg(g->device);
+    TEC_TRY(ensure_k4(g));
+    TEC_TRY(ensure_uoff(g));
+    TEC_CUDA(launch_export(g->off, g->col, g->deg, g->ooff, g->ocol, g->k4, g->keep, g->n, g->nnz, g->uoff,
+                           nullptr, nullptr, k4_out, nullptr, nullptr, 0, nullptr, g->ctr, g->stream));
+    return TEC_OK;
+}
+
 tec_status tec_edge_weights(tec_graph *g, tec_measure measure, double *w_out) {
     clear_error();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
-    if (measure < TEC_TECTONIC || measure > TEC_K3) return set_error(TEC_EINVAL, "unknown measure %d", (int)measure);
+    if (measure < TEC_TECTONIC || measure > TEC_K4) return set_error(TEC_EINVAL, "unknown measure %d", (int)measure);
     if (!w_out && g->m > 0) return set_error(TEC_EINVAL, "w_out is NULL");
     DeviceGuard dg(g->device);
-    TEC_TRY(ensure_support(g));
+    const uint32_t *cts = nullptr;
+    int cmp = (int)measure;
+    TEC_TRY(measure_counts(g, (int)measure, &cts, &cmp));
     TEC_TRY(ensure_uoff(g));
-    TEC_CUDA(launch_export(g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->n, g->nnz, g->uoff,
-                           nullptr, nullptr, nullptr, nullptr, w_out, (int)measure, nullptr, g->ctr, g->stream));
+    TEC_CUDA(launch_export(g->off, g->col, g->deg, g->ooff, g->ocol, cts, g->keep, g->n, g->nnz, g->uoff,
+                           nullptr, nullptr, nullptr, nullptr, w_out, cmp, nullptr, g->ctr, g->stream));
     return TEC_OK;
 }
 
@@ -512,10 +560,12 @@ tec_status tec_prune(tec_graph *g, tec_measure measure, int64_t p, int64_t q, ui
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     TEC_TRY(check_threshold((int)measure, p, q));
     DeviceGuard dg(g->device);
-    TEC_TRY(ensure_support(g));
+    const uint32_t *cts = nullptr;
+    int cmp = (int)measure;
+    TEC_TRY(measure_counts(g, (int)measure, &cts, &cmp));
     TEC_TRY(reset_counter(g, C_KEPT));
-    PruneArgs a{(int)measure, p, q, false};
-    TEC_CUDA(launch_prune(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, a, g->keep, g->parent, g->ctr, g->stream));
+    PruneArgs a{cmp, p, q, false};
+    TEC_CUDA(launch_prune(g->ooff, g->ocol, g->deg, cts, g->n, g->m, a, g->keep, g->parent, g->ctr, g->stream));
     g->pruned = true;
     g->hooked = false;
     g->last_measure = (int)measure;
@@ -649,7 +699,9 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
     int32_t *lu = list ? g->msf_u : nullptr, *lv = list ? g->msf_v : nullptr, *lc = list ? g->msf_cnt : nullptr;
     unsigned long long *lk = list ? g->msf_k : nullptr;
     if (!g->msf_changed) TEC_TRY(dalloc(&g->msf_changed, 64, "forest round flags"));
-    TEC_TRY(ensure_support(g));
+    const uint32_t *cts = nullptr;
+    int cmp = (int)measure;
+    TEC_TRY(measure_counts(g, (int)measure, &cts, &cmp));
     // From here on only kernels and memsets on the graph's stream: with the
     // buffers above allocated and ncomp_out NULL, a caller can capture the
     // whole sweep in a CUDA graph.
@@ -664,7 +716,7 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
     TEC_CUDA(launch_cc_init(g->parent, g->n, s));
     if (g->n > 0) TEC_CUDA(cudaMemsetAsync(g->best, 0, (size_t)g->n * sizeof(unsigned long long), s));
     TEC_CUDA(cudaMemsetAsync(g->msf_changed, 0, 64 * sizeof(unsigned long long), s));
-    TEC_CUDA(launch_levels(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, (int)measure, g->thr, g->thr + k, k, wide,
+    TEC_CUDA(launch_levels(g->ooff, g->ocol, g->deg, cts, g->n, g->m, cmp, g->thr, g->thr + k, k, wide,
                            g->lvl, g->best, lu, lv, lk, lc, g->ctr, s));
     for (int round = 0; round < rounds; ++round) {
         const unsigned long long *prev = round > 0 ? g->msf_changed + round - 1 : nullptr;
@@ -722,8 +774,10 @@ tec_status tec_sweep_stats(tec_graph *g, tec_measure measure, const int64_t *p, 
     if (!g->st_cnt_n) TEC_TRY(dalloc(&g->st_cnt_n, 2 * cl, "component sizes"));
     if (!g->st_cnt_v) TEC_TRY(dalloc(&g->st_cnt_v, 2 * cl, "component volumes"));
     TEC_CUDA(cudaMemcpyAsync(g->thr, hthr.data(), hthr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
-    TEC_TRY(ensure_support(g));
-    TEC_CUDA(launch_sweep_stats(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, (int)measure, g->thr, g->thr + 127, k,
+    const uint32_t *cts = nullptr;
+    int cmp = (int)measure;
+    TEC_TRY(measure_counts(g, (int)measure, &cts, &cmp));
+    TEC_CUDA(launch_sweep_stats(g->ooff, g->ocol, g->deg, cts, g->n, g->m, cmp, g->thr, g->thr + 127, k,
                                 order.data(), wide, labels, seg_off, nseg, g->st_hist, g->st_cnt_n, g->st_cnt_v, cl,
                                 g->st_sums, stats_out, g->ctr, g->stream));
     return TEC_OK;
@@ -746,7 +800,7 @@ tec_status tec_prune_components_batch(tec_graph *g, tec_measure measure, const i
                                       const int64_t *seg_off, int nseg, int32_t *labels_out, int64_t *ncomp_out) {
     clear_error();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
-    if (measure < TEC_TECTONIC || measure > TEC_K3) return set_error(TEC_EINVAL, "unknown measure %d", (int)measure);
+    if (measure < TEC_TECTONIC || measure > TEC_K4) return set_error(TEC_EINVAL, "unknown measure %d", (int)measure);
     if (!p || !q || !seg_off || nseg < 1) return set_error(TEC_EINVAL, "thresholds and segment table are required");
     if (!labels_out && g->n > 0) return set_error(TEC_EINVAL, "labels_out is NULL");
     DeviceGuard dg(g->device);
@@ -757,10 +811,12 @@ tec_status tec_prune_components_batch(tec_graph *g, tec_measure measure, const i
         TEC_TRY(dalloc(&g->sw_ncomp, nseg, "component counts"));
         g->sw_ncomp_cap = nseg;
     }
-    TEC_TRY(ensure_support(g));
+    const uint32_t *cts = nullptr;
+    int cmp = (int)measure;
+    TEC_TRY(measure_counts(g, (int)measure, &cts, &cmp));
     TEC_TRY(reset_counter(g, C_KEPT));
     TEC_CUDA(launch_cc_init(g->parent, g->n, g->stream));
-    TEC_CUDA(launch_prune_seg(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, (int)measure, p, q, seg_off, nseg, true,
+    TEC_CUDA(launch_prune_seg(g->ooff, g->ocol, g->deg, cts, g->n, g->m, cmp, p, q, seg_off, nseg, true,
                               g->keep, g->parent, g->ctr, g->stream));
     g->pruned = g->hooked = true;
     TEC_CUDA(cudaMemsetAsync(g->sw_ncomp, 0, (size_t)nseg * sizeof(unsigned long long), g->stream));

@@ -201,6 +201,12 @@ cudaError_t launch_sweep_stats(const int64_t *ooff, const int32_t *ocol, const i
 cudaError_t launch_rules(const tec_sweep_stat *stats, int k, int nseg, const int *order, int rule, int32_t *best,
                          cudaStream_t s);
 
+// k4.cu: K4 participation per oriented edge (t = triangle counts, next = one
+// work counter), saturating at 2^32 - 1.
+cudaError_t launch_k4(const int64_t *off, const int32_t *col, const int64_t *ooff, const int32_t *ocol,
+                      const uint32_t *t, int64_t n, int64_t m, unsigned long long *next, uint32_t *k4,
+                      unsigned long long *ctr, int num_sms, cudaStream_t s);
+
 // cc.cu
 cudaError_t launch_cc_init(int32_t *parent, int64_t n, cudaStream_t s);
 cudaError_t launch_cc_hook(const int64_t *ooff, const int32_t *ocol, const uint32_t *keep,
@@ -368,6 +374,11 @@ struct tec_graph {
     unsigned long long *core_hist = nullptr;  // 33 degree bins + 2 meta words
     int core_state = 0;                   // 0 untried, 1 available, -1 unavailable
     bool core_enabled = true;             // tec_set_core_staging
+    // K4 participation per oriented edge (saturating), allocated on first use
+    uint32_t *k4 = nullptr;
+    unsigned long long *k4_next = nullptr;
+    unsigned long long support_epoch = 0; // bumped whenever the triangle counts are recomputed
+    unsigned long long k4_epoch = ~0ull;  // support_epoch the K4 counts belong to
     unsigned long long *msf_changed = nullptr;  // 64 per-round "a tree grew" flags
     int32_t *fu = nullptr, *fv = nullptr; // n: forest edges bucketed by level
     unsigned long long *bucket = nullptr; // 3k+4 bucket counts / offsets / cursors

@@ -18,6 +18,7 @@ TECTONIC = 0
 TW = 1
 JACCARD = 2
 K3 = 3
+K4 = 4
 HOST_PTR = 0x1
 VALIDATE = 0x2
 
@@ -78,6 +79,7 @@ SIGNATURES = {
     "tec_sweep_stats": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "tec_rule_of_thumb": ([_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
     "tec_set_core_staging": ([_P, ctypes.c_int], ctypes.c_int),
+    "tec_edge_k4": ([_P, _P], ctypes.c_int),
     "tec_components_noalloc": ([_I64, _I64, _P, _P, _P, _P, _PI64, _P], ctypes.c_int),
 }
 
@@ -270,6 +272,13 @@ class Graph:
         w = self._empty(self.m, torch.int32) if wedges else None
         check(self._lib.tec_edge_support(self._h, _ptr(t), _ptr(w)))
         return t, w
+
+    def edge_k4(self):
+        """4-cliques containing each edge (canonical order, CUDA uint32 as int32 storage)."""
+        torch = _torch()
+        out = self._empty(self.m, torch.int32)
+        check(self._lib.tec_edge_k4(self._h, _ptr(out)))
+        return out
 
     def edge_weights(self, measure: int = TECTONIC):
         torch = _torch()

@@ -51,8 +51,14 @@ def check_all(tec, off, col, thresholds):
     w_jac = g.edge_weights(tec.JACCARD).cpu().numpy()
     assert np.array_equal(w_jac.view(np.uint64), O.jaccard_weights(t, uni).view(np.uint64))
     assert np.array_equal(g.edge_weights(tec.K3).cpu().numpy(), O.k3_scores(t).astype(np.float64))
+    # K4 (a costly oracle on large hub-heavy graphs): when asked for, or on graphs up to 2M edges
+    k4 = None
+    if any(th[0] == O.K4 for th in thresholds) or len(eu) <= 2_000_000:
+        k4 = O.edge_k4(off, col, eu, ev, nthreads=O.threads_available())
+        assert np.array_equal(_u32(g.edge_k4()).astype(np.uint64), np.minimum(k4, 0xFFFFFFFF))
+        assert np.array_equal(g.edge_weights(tec.K4).cpu().numpy(), k4.astype(np.float64))
     for measure, p, q in thresholds:
-        keep, kept = O.prune(measure, off, eu, ev, t, uni, p, q)
+        keep, kept = O.prune(measure, off, eu, ev, t, uni, p, q, k4)
         labels, nc = O.components(n, eu, ev, keep)
         gkeep, gkept = g.prune(measure, p, q, mask=True)
         assert gkept == kept
@@ -72,7 +78,7 @@ def check_all(tec, off, col, thresholds):
 
 
 STD = [(O.TECTONIC, 1, 10), (O.TECTONIC, 3, 50), (O.TW, -30, 1), (O.TW, 0, 1), (O.TW, 3, 50),
-       (O.JACCARD, 1, 5), (O.JACCARD, 1, 2), (O.K3, 3, 1), (O.K3, 7, 2)]
+       (O.JACCARD, 1, 5), (O.JACCARD, 1, 2), (O.K3, 3, 1), (O.K3, 7, 2), (O.K4, 1, 1), (O.K4, 5, 2)]
 
 
 @pytest.mark.parametrize("name,graph", [
@@ -271,4 +277,28 @@ def test_jaccard_sweep_and_prop1_on_device(tec):
     for i, (p, q) in enumerate(zip(ps, qs)):
         tl, _ = g.full_pass(tec.TECTONIC, p, p + q)
         assert torch.equal(tl, lab[i])
+    g.free()
+
+
+def test_k4_large_common_neighbourhoods_and_sweep(tec):
+    """K4 on a book graph: spine edge (0, 1), pages 2..1101 adjacent to both
+    ends and joined in a path, so C(0, 1) holds 1100 ids (more than a warp's
+    shared slice: the unstored path) and K4(0, 1) = 1099 path edges; then a
+    K4 sweep against the oracle."""
+    from graphgen import csr_from_pairs
+    pages = np.arange(2, 1102)
+    u = np.concatenate([[0], np.zeros(1100, int), np.ones(1100, int), pages[:-1]])
+    v = np.concatenate([[1], pages, pages, pages[1:]])
+    off, col = csr_from_pairs(1102, u, v)
+    check_all(tec, off, col, [(O.K4, 1, 1), (O.K4, 2, 1), (O.K4, 1099, 1), (O.TECTONIC, 1, 10)])
+    g = _gpu_graph(tec, off, col)
+    eu, ev = O.edge_list(off, col)
+    assert _u32(g.edge_k4())[(eu == 0) & (ev == 1)][0] == 1099
+    g.free()
+    off, col, _ = planted_partition(4, 300, 0.08, 0.004, seed=5)
+    g = _gpu_graph(tec, off, col)
+    ps, qs = [0, 1, 2, 3, 5, 8], [1] * 6
+    lab, nc = g.sweep(tec.K4, ps, qs)
+    ol, onc = O.sweep(off, col, O.K4, ps, qs)
+    assert np.array_equal(lab.cpu().numpy(), ol) and np.array_equal(nc, onc)
     g.free()

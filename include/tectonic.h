@@ -248,6 +248,16 @@ typedef enum { TEC_RULE_LARGEST_JUMP = 0, TEC_RULE_MODULARITY = 1 } tec_rule;
 tec_status tec_rule_of_thumb(const tec_sweep_stat *stats, const int64_t *p, const int64_t *q, int k, int nseg,
                              tec_rule rule, int32_t *best_out, void *stream);
 
+/* Precision, recall and F1 of Sec. IV-A for k labelings against reference
+ * blocks (same inputs as tec_ari): every found community S is matched to the
+ * block C of largest Jaccard |C n S| / |C u S| (the lowest block id on ties),
+ * p = |C n S| / |S|, r = |C n S| / |C|, and the three scores are the
+ * size-weighted means of p, r and 2pr / (p + r).  prf_out: device,
+ * k x nseg x 3 float64 (precision, recall, F1).  Precision is a ratio of exact
+ * integers; recall and F1 are float64 sums (summation order unspecified). */
+tec_status tec_prf(tec_graph *g, int k, const int32_t *labels, const int32_t *truth, const int64_t *seg_off, int nseg,
+                   double *prf_out);
+
 /* For each of nseg graphs, the first of k rows of ari (device, k x nseg, as
  * written by tec_ari) with the highest value: best (device, nseg int32, row
  * index) and, if not NULL, that value (device, nseg float64), on `stream`. */

@@ -67,6 +67,7 @@ void free_graph_memory(tec_graph *g) {
                     g->fu, g->fv, g->bucket, g->thr, g->sw_ncomp, g->seg_hist, g->ari_sums,
                     g->ari_size, g->ari_keys, g->ari_cnt, g->msf_u, g->msf_v, g->msf_k, g->msf_cnt, g->msf_changed,
                     g->core_of, g->pv2, g->ctasks, g->core_tc, g->core_hist, g->k4, g->k4_next,
+                    g->prf_best, g->prf_bestb, g->prf_sums,
                     g->st_hist, g->st_sums, g->st_cnt_n, g->st_cnt_v, g->ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -307,6 +308,36 @@ tec_status tec_ari(tec_graph *g, int k, const int32_t *labels, const int32_t *tr
     g->ari_n = g->n;
     TEC_CUDA(launch_ari(labels, k, truth, g->n, seg_off, nseg, g->seg_hist, g->ari_size, std::max<int64_t>(g->n_cap, 1),
                         g->ari_keys, g->ari_cnt, tsize, g->ari_sums, ari_out, &g->ari_tag, g->ctr, g->stream));
+    return TEC_OK;
+}
+
+tec_status tec_prf(tec_graph *g, int k, const int32_t *labels, const int32_t *truth, const int64_t *seg_off, int nseg,
+                   double *prf_out) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (k < 1) return set_error(TEC_EINVAL, "k must be >= 1");
+    if ((!labels || !truth) && g->n > 0) return set_error(TEC_EINVAL, "labels or truth is NULL");
+    if (!prf_out) return set_error(TEC_EINVAL, "prf_out is NULL");
+    if (seg_off && nseg < 1) return set_error(TEC_EINVAL, "nseg must be >= 1 with a segment table");
+    DeviceGuard dg(g->device);
+    const int ns = seg_off ? nseg : 1;
+    TEC_TRY(ensure_seg_scratch(g, ns));
+    const int64_t tsize = (int64_t)1 << ari_table_bits(g->n_cap);
+    const int64_t ncap = std::max<int64_t>(g->n_cap, 1);
+    if (!g->ari_size) {
+        TEC_TRY(dalloc(&g->ari_size, 2 * ncap, "component sizes"));
+        TEC_TRY(dalloc(&g->ari_keys, tsize, "cell keys"));
+        TEC_TRY(dalloc(&g->ari_cnt, tsize, "cell counts"));
+        g->ari_tag = ~0ull;
+    }
+    if (!g->prf_best) TEC_TRY(dalloc(&g->prf_best, ncap, "best matches"));
+    if (!g->prf_bestb) TEC_TRY(dalloc(&g->prf_bestb, ncap, "matched blocks"));
+    TEC_TRY(grow(&g->prf_sums, &g->prf_sums_cap, (int64_t)3 * ns * ARI_CHUNK, "P/R/F1 sums"));
+    if (g->ari_n != g->n) g->ari_tag = ~0ull;
+    g->ari_n = g->n;
+    TEC_CUDA(launch_prf(labels, k, truth, g->n, seg_off, nseg, g->seg_hist, g->ari_size, ncap, g->ari_keys, g->ari_cnt,
+                        tsize, g->ari_sums, g->prf_best, g->prf_bestb, g->prf_sums, prf_out, &g->ari_tag, g->ctr,
+                        g->stream));
     return TEC_OK;
 }
 

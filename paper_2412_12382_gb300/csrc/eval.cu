@@ -312,6 +312,143 @@ __global__ void __launch_bounds__(256) k_ari_cells(const int32_t *labels, const 
     if (lane == 0 && pend) atomicAdd(&sums[2 * pend_s], pend);
 }
 
+// ---------------------------------------------------------------- P/R/F1
+//
+// Sec. IV-A: each found community S (a component) is matched to the reference
+// block C of largest Jaccard |C n S| / |C u S| (the lowest block id on ties),
+// p = |C n S| / |S|, r = |C n S| / |C|, and precision, recall and F1 are the
+// size-weighted means of p, r and 2pr/(p + r).  Per level: component sizes
+// (the ARI sizes pass), every (root, block) cell counted (singletons
+// included), each vertex raising its root's best Jaccard (the double of the
+// same division the definition writes, so ties are exact), the lowest block
+// reaching it, and one term per community.
+
+// Slot of cell key ck at this level, or -1 (no claim: a cell is found at or
+// before the first slot of an older level along its probe sequence).
+__device__ __forceinline__ int64_t cell_find(const unsigned long long *keys, int bits, unsigned long long tag,
+                                             unsigned long long ck) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    const unsigned long long want = (tag << TAG_SHIFT) | ck;
+    uint64_t h = hkey(ck, bits);
+    for (uint64_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+        const unsigned long long cur = __ldcg(&keys[h]);
+        if (cur == want) return (int64_t)h;
+        if ((cur >> TAG_SHIFT) != tag) return -1;
+    }
+    return -1;
+}
+
+struct PrfVertex {
+    bool valid;
+    int s;
+    int32_t root;
+    int b;
+};
+
+// Root and block of vertex x (x0 the warp's first vertex), for the P/R/F1 passes.
+__device__ __forceinline__ PrfVertex prf_vertex(const int32_t *labels, const int32_t *truth, int64_t n,
+                                                const int64_t *seg_off, int nseg, int64_t x0, int64_t x) {
+    PrfVertex v{false, 0, -1, -1};
+    if (x >= n) return v;
+    v.s = seg_off ? warp_seg_of(seg_off, nseg, x0, x) : 0;
+    const int64_t r = (seg_off ? seg_off[v.s] : 0) + labels[x];
+    const int b = truth[x];
+    if (r < 0 || r >= n || b < 0 || b >= NBINS) return v;   // reported by the sizes pass / block sizes
+    v.valid = true;
+    v.root = (int32_t)r;
+    v.b = b;
+    return v;
+}
+
+__device__ __forceinline__ double prf_jaccard(unsigned long long inter, unsigned int size, unsigned int csize) {
+    return (double)inter / (double)((unsigned long long)size + csize - inter);
+}
+
+__global__ void __launch_bounds__(256) k_prf_cells(const int32_t *labels, const int32_t *truth, int64_t n,
+                                                   const int64_t *seg_off, int nseg, unsigned long long tag,
+                                                   unsigned long long *keys, unsigned long long *cnt, int bits,
+                                                   unsigned long long *ctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const unsigned lane = lane_id();
+    for (int64_t x0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); x0 < n; x0 += stride) {
+        const int64_t x = x0 + lane;
+        const PrfVertex v = prf_vertex(labels, truth, n, seg_off, nseg, x0 < n ? x0 : n - 1, x);
+        const unsigned long long key = v.valid ? ((unsigned long long)v.root << 6) | (unsigned long long)v.b : ~0ull;
+        const unsigned same = key_group(v.valid, key);
+        if (v.valid && lane == (unsigned)(__ffs(same) - 1)) {
+            const int64_t slot = cell_slot(keys, bits, tag, key);
+            if (slot < 0) flag_status(ctr, ST_BADGRAPH);
+            else tagged_add(&cnt[slot], tag, (unsigned long long)__popc(same));
+        }
+    }
+}
+
+// PICK = false: best[root] = max over its cells of the Jaccard bits;
+// PICK = true: bestb[root] = lowest block whose cell reaches best[root].
+template <bool PICK>
+__global__ void __launch_bounds__(256) k_prf_best(const int32_t *labels, const int32_t *truth, int64_t n,
+                                                  const int64_t *seg_off, int nseg, unsigned long long tag,
+                                                  const unsigned long long *keys, const unsigned long long *cnt,
+                                                  int bits, const unsigned int *size, const unsigned int *bsz,
+                                                  unsigned long long *best, unsigned int *bestb) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const unsigned lane = lane_id();
+    for (int64_t x0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); x0 < n; x0 += stride) {
+        const int64_t x = x0 + lane;
+        const PrfVertex v = prf_vertex(labels, truth, n, seg_off, nseg, x0 < n ? x0 : n - 1, x);
+        if (!v.valid) continue;
+        const unsigned long long key = ((unsigned long long)v.root << 6) | (unsigned long long)v.b;
+        const int64_t slot = cell_find(keys, bits, tag, key);
+        if (slot < 0) continue;
+        const unsigned long long inter = __ldcg(&cnt[slot]) & CNT_MASK;
+        const double j = prf_jaccard(inter, size[v.root], bsz[(int64_t)v.s * NBINS + v.b]);
+        const unsigned long long jb = (unsigned long long)__double_as_longlong(j);   // j >= 0: bits order as values
+        if (!PICK) atomicMax(&best[v.root], jb);
+        else if (jb == __ldcg(&best[v.root])) atomicMin(&bestb[v.root], (unsigned int)v.b);
+    }
+}
+
+// One term per community (every label value r with size[r] > 0; r indexes
+// the graph the labels are relative to): sums[3 s] += |C n S| (integer),
+// sums[3 s + 1] += r |S|, sums[3 s + 2] += 2pr/(p + r) |S| (doubles, as bit
+// patterns).
+__global__ void __launch_bounds__(256) k_prf_sum(int64_t n, const int64_t *seg_off, int nseg,
+                                                 unsigned long long tag, const unsigned long long *keys,
+                                                 const unsigned long long *cnt, int bits, const unsigned int *size,
+                                                 const unsigned int *bsz, const unsigned int *bestb,
+                                                 unsigned long long *sums) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const unsigned lane = lane_id();
+    for (int64_t x0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); x0 < n; x0 += stride) {
+        const int64_t x = x0 + lane;
+        if (x >= n || size[x] == 0u) continue;                             // communities only
+        const int s = seg_off ? warp_seg_of(seg_off, nseg, x0, x) : 0;
+        const unsigned int b = bestb[x];
+        if (b >= (unsigned)NBINS) continue;
+        const int64_t slot = cell_find(keys, bits, tag, ((unsigned long long)x << 6) | b);
+        if (slot < 0) continue;
+        const unsigned long long inter = __ldcg(&cnt[slot]) & CNT_MASK;
+        const unsigned int sz = size[x], cs = bsz[(int64_t)s * NBINS + b];
+        const double p = (double)inter / (double)sz, r = (double)inter / (double)cs;
+        atomicAdd(&sums[3 * s], inter);
+        atomicAdd(reinterpret_cast<double *>(&sums[3 * s + 1]), r * (double)sz);
+        atomicAdd(reinterpret_cast<double *>(&sums[3 * s + 2]), (2.0 * p * r / (p + r)) * (double)sz);
+    }
+}
+
+__global__ void k_prf_final(const unsigned long long *sums, const int64_t *seg_off, int nseg, int levels,
+                            int64_t n_all, double *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)levels * nseg) return;
+    const int s = (int)(i % nseg);
+    const int64_t nv = seg_off ? seg_off[s + 1] - seg_off[s] : n_all;
+    const double inv = nv > 0 ? 1.0 / (double)nv : 0.0;
+    out[3 * i] = nv > 0 ? (double)sums[3 * i] / (double)nv : 0.0;
+    out[3 * i + 1] = __longlong_as_double((long long)sums[3 * i + 1]) * inv;
+    out[3 * i + 2] = __longlong_as_double((long long)sums[3 * i + 2]) * inv;
+    (void)inv;
+}
+
 __device__ double i128_to_double(__int128 v) {
     const bool neg = v < 0;
     unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
@@ -423,6 +560,59 @@ cudaError_t launch_ari(const int32_t *labels, int k, const int32_t *truth, int64
         const int64_t cells = (int64_t)levels * ns;
         k_ari_final<<<(unsigned)ceil_div(cells, 128), 128, 0, s>>>(sums, bsz, seg_off, ns, levels, n,
                                                                    out + (int64_t)L0 * ns);
+        ++launched;
+    }
+    count_launches(launched);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prf(const int32_t *labels, int k, const int32_t *truth, int64_t n, const int64_t *seg_off, int nseg,
+                       unsigned int *bsz, unsigned int *size, int64_t size_len, unsigned long long *keys,
+                       unsigned long long *cnt, int64_t tsize, unsigned long long *scratch_sums,
+                       unsigned long long *best, unsigned int *bestb, unsigned long long *sums, double *out,
+                       unsigned long long *tag, unsigned long long *ctr, cudaStream_t s) {
+    const int ns = seg_off ? nseg : 1;
+    const int bits = ari_table_bits(n);
+    cudaError_t e = cudaMemsetAsync(bsz, 0, (size_t)ns * NBINS * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    int launched = 0;
+    if (n > 0) {
+        k_block_sizes<<<(unsigned)ceil_div(n, BS_CHUNK), 256, 0, s>>>(truth, n, seg_off, ns, bsz, ctr);
+        ++launched;
+    }
+    for (int L0 = 0; L0 < k; L0 += ARI_CHUNK) {
+        const int levels = k - L0 < ARI_CHUNK ? k - L0 : ARI_CHUNK;
+        if ((e = cudaMemsetAsync(sums, 0, (size_t)3 * ns * levels * sizeof(unsigned long long), s)) != cudaSuccess)
+            return e;
+        for (int L = L0; L < L0 + levels && n > 0; ++L) {
+            if (*tag >= TAG_LIMIT) {             // first use, or the tag would wrap: zero every word
+                if ((e = cudaMemsetAsync(size, 0, (size_t)2 * size_len * sizeof(unsigned int), s)) != cudaSuccess)
+                    return e;
+                if ((e = cudaMemsetAsync(keys, 0, (size_t)tsize * sizeof(unsigned long long), s)) != cudaSuccess)
+                    return e;
+                if ((e = cudaMemsetAsync(cnt, 0, (size_t)tsize * sizeof(unsigned long long), s)) != cudaSuccess)
+                    return e;
+                *tag = 0;
+            }
+            const unsigned long long t = ++*tag;
+            unsigned int *cur = size + (t & 1ull) * size_len, *prev = size + ((t & 1ull) ^ 1ull) * size_len;
+            const int32_t *lab = labels + (int64_t)L * n;
+            if ((e = cudaMemsetAsync(best, 0, (size_t)n * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(bestb, 0xFF, (size_t)n * sizeof(unsigned int), s)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(scratch_sums, 0, (size_t)2 * ns * sizeof(unsigned long long), s)) != cudaSuccess)
+                return e;
+            const unsigned grid = vertex_pass_grid(n), gv = grid_for(n);
+            unsigned long long *ls = sums + (int64_t)3 * ns * (L - L0);
+            k_ari_sizes<<<grid, 256, 0, s>>>(lab, n, seg_off, ns, cur, prev, scratch_sums, ctr);
+            k_prf_cells<<<gv, 256, 0, s>>>(lab, truth, n, seg_off, ns, t, keys, cnt, bits, ctr);
+            k_prf_best<false><<<gv, 256, 0, s>>>(lab, truth, n, seg_off, ns, t, keys, cnt, bits, cur, bsz, best, bestb);
+            k_prf_best<true><<<gv, 256, 0, s>>>(lab, truth, n, seg_off, ns, t, keys, cnt, bits, cur, bsz, best, bestb);
+            k_prf_sum<<<gv, 256, 0, s>>>(n, seg_off, ns, t, keys, cnt, bits, cur, bsz, bestb, ls);
+            launched += 5;
+        }
+        const int64_t cells = (int64_t)levels * ns;
+        k_prf_final<<<(unsigned)ceil_div(cells, 128), 128, 0, s>>>(sums, seg_off, ns, levels, n,
+                                                                   out + (int64_t)3 * L0 * ns);
         ++launched;
     }
     count_launches(launched);

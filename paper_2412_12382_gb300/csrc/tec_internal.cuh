@@ -207,6 +207,14 @@ cudaError_t launch_k4(const int64_t *off, const int32_t *col, const int64_t *oof
                       const uint32_t *t, int64_t n, int64_t m, unsigned long long *next, uint32_t *k4,
                       unsigned long long *ctr, int num_sms, cudaStream_t s);
 
+// P/R/F1 of Sec. IV-A (shares the ARI counters, tables and tag; best / bestb:
+// n each; scratch_sums: 2 x nseg; sums: 3 x nseg x ARI_CHUNK; out: k x nseg x 3).
+cudaError_t launch_prf(const int32_t *labels, int k, const int32_t *truth, int64_t n, const int64_t *seg_off, int nseg,
+                       unsigned int *bsz, unsigned int *size, int64_t size_len, unsigned long long *keys,
+                       unsigned long long *cnt, int64_t tsize, unsigned long long *scratch_sums,
+                       unsigned long long *best, unsigned int *bestb, unsigned long long *sums, double *out,
+                       unsigned long long *tag, unsigned long long *ctr, cudaStream_t s);
+
 // cc.cu
 cudaError_t launch_cc_init(int32_t *parent, int64_t n, cudaStream_t s);
 cudaError_t launch_cc_hook(const int64_t *ooff, const int32_t *ocol, const uint32_t *keep,
@@ -394,6 +402,11 @@ struct tec_graph {
     unsigned long long *ari_keys = nullptr; // 2^bits level-tagged cell keys
     unsigned long long *ari_cnt = nullptr;  // 2^bits level-tagged cell counts
     unsigned long long ari_tag = 0;         // last level tag used in the arrays above
+    // P/R/F1 scratch
+    unsigned long long *prf_best = nullptr;     // n_cap best Jaccard bits per root
+    unsigned int *prf_bestb = nullptr;          // n_cap matched block per root
+    unsigned long long *prf_sums = nullptr;     // 3 x nseg x ARI_CHUNK
+    int64_t prf_sums_cap = 0;
     // sweep statistics scratch, grown on demand
     unsigned long long *st_hist = nullptr;  // nseg x 2 (k + 1) level / join-level histograms
     int64_t st_hist_cap = 0;

@@ -80,6 +80,7 @@ SIGNATURES = {
     "tec_rule_of_thumb": ([_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
     "tec_set_core_staging": ([_P, ctypes.c_int], ctypes.c_int),
     "tec_edge_k4": ([_P, _P], ctypes.c_int),
+    "tec_prf": ([_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "tec_components_noalloc": ([_I64, _I64, _P, _P, _P, _P, _PI64, _P], ctypes.c_int),
 }
 
@@ -362,6 +363,17 @@ class Graph:
         check(self._lib.tec_pick_threshold(self._h, picker._h, _ptr(seg_off) if seg_off is not None else None, nseg,
                                            int(bf16), _ptr(p), _ptr(q)))
         return p, q
+
+    def prf(self, labels, truth, seg_off=None):
+        """Precision, recall, F1 (Sec. IV-A) of each row of `labels` (k x n) against `truth`:
+        (k, nseg, 3) float64 tensor."""
+        torch = _torch()
+        k = labels.shape[0] if labels.dim() == 2 else 1
+        nseg = 0 if seg_off is None else seg_off.numel() - 1
+        out = torch.empty((k, max(nseg, 1), 3), dtype=torch.float64, device="cuda")
+        check(self._lib.tec_prf(self._h, k, _ptr(labels.contiguous()), _ptr(truth.contiguous()),
+                                _ptr(seg_off) if seg_off is not None else None, nseg, _ptr(out)))
+        return out
 
     def prune_components_batch(self, measure: int, p, q, seg_off, labels=None, count: bool = True):
         """Per-graph thresholds p[s]/q[s] (CUDA int64): local labels (n) and components per graph."""

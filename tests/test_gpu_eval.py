@@ -122,3 +122,46 @@ def test_ari_many_levels_tiny_segments_repeated(tec):
                 ref = O.ari(labs[L, seg[i]:seg[i + 1]], truth[seg[i]:seg[i + 1]])
                 assert abs(ari[L, i] - ref) <= 2e-15, (L, i, ari[L, i], ref)
     g.free()
+
+
+
+def test_precision_recall_f1_against_oracle(tec):
+    """Sec. IV-A scores of random labelings, of the planted blocks themselves
+    (1, 1, 1) and of a sweep over a batch, against the oracle: precision to
+    1e-15 (a ratio of exact integers), recall and F1 to 1e-12 relative
+    (float64 sums in another order)."""
+    import torch
+    rng = np.random.default_rng(9)
+    off, col = small.gnp(400, 0.04, rng)
+    g = _graph(tec, off, col)
+    n = 400
+    truth = rng.integers(0, 7, n).astype(np.int32)
+    labs = np.stack([rng.integers(0, k, n) for k in (1, 3, 20, 400)] + [np.arange(n), truth]).astype(np.int32)
+    got = g.prf(torch.from_numpy(labs).cuda(), torch.from_numpy(truth).cuda()).cpu().numpy()[:, 0, :]
+    for L in range(len(labs)):
+        ref = O.precision_recall_f1(truth, labs[L])
+        assert abs(got[L, 0] - ref[0]) <= 1e-15
+        assert np.allclose(got[L, 1:], ref[1:], rtol=1e-12, atol=0)
+    assert np.array_equal(got[-1], [1.0, 1.0, 1.0])
+    g.free()
+    sizes = [[60, 80, 50], [120, 40], [30] * 6]
+    graphs, truths = [], []
+    for s, sz in enumerate(sizes):
+        P = np.full((len(sz), len(sz)), 0.02)
+        np.fill_diagonal(P, 0.3)
+        o, c, blk = sbm_csr(sz, P, seed=60 + s)
+        graphs.append((o, c))
+        truths.append(blk)
+    off, col, seg = disjoint_union(graphs)
+    tr = np.concatenate(truths).astype(np.int32)
+    g = _graph(tec, off, col)
+    segd = torch.from_numpy(seg).cuda()
+    lab, _ = g.sweep(O.TECTONIC, [p for p, _ in GRID], [q for _, q in GRID], seg_off=segd)
+    got = g.prf(lab, torch.from_numpy(tr).cuda(), segd).cpu().numpy()
+    labh = lab.cpu().numpy()
+    for gi in range(len(graphs)):
+        for L in range(0, 64, 3):
+            ref = O.precision_recall_f1(truths[gi], labh[L, seg[gi]:seg[gi + 1]])
+            assert abs(got[L, gi, 0] - ref[0]) <= 1e-15
+            assert np.allclose(got[L, gi, 1:], ref[1:], rtol=1e-12, atol=0), (gi, L)
+    g.free()

@@ -304,7 +304,7 @@ def bench_picker(reps=3):
     got = g.ari(plab[None, :], truth, seg)[0]
     ari_all = g.ari(lab_all, truth, seg)
     fixed_level = int(meta.get("eval", {}).get("fixed_level", 8)) - 1
-    # the paper's rules of thumb (Sec. IV-E) on the same sweep, as baselines
+    # the paper's rules of thumb (Sec. IV-D) on the same sweep, as baselines
     stats = g.sweep_stats(TECTONIC, PK.GRID_P, PK.GRID_Q, lab_all, seg)
     cols = torch.arange(nseg, device="cuda")
     rule_ari = {}

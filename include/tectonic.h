@@ -189,7 +189,7 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
  * (bin = min(63, floor(128 t / (deg u + deg v)))), divided by the graph's edge
  * count m, then ln(2m/n) and ln(m).  feat_out: device, nseg x 66 float32
  * (rows of zeros for graphs without edges).  Runs tec_support if needed.  The
- * paper picks thresholds by rules of thumb (Sec. IV-E); these features feed
+ * paper picks thresholds by rules of thumb (Sec. IV-D); these features feed
  * the learned picker that replaces them. */
 tec_status tec_features(tec_graph *g, const int64_t *seg_off, int nseg, float *feat_out);
 
@@ -214,7 +214,7 @@ tec_status tec_ari(tec_graph *g, int k, const int32_t *labels, const int32_t *tr
 tec_status tec_prune_components_batch(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q,
                                       const int64_t *seg_off, int nseg, int32_t *labels_out, int64_t *ncomp_out);
 
-/* Per-threshold statistics of a sweep, the quantities Sec. IV-E plots
+/* Per-threshold statistics of a sweep, the quantities Sec. IV-D plots
  * against the threshold (Fig. 6), for every graph of a batch (the whole graph
  * if seg_off is NULL). */
 typedef struct tec_sweep_stat {
@@ -237,7 +237,7 @@ typedef struct tec_sweep_stat {
 tec_status tec_sweep_stats(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q, int k,
                            const int32_t *labels, const int64_t *seg_off, int nseg, tec_sweep_stat *stats_out);
 
-/* The threshold rules of thumb of Sec. IV-E, per graph, from k x nseg
+/* The threshold rules of thumb of Sec. IV-D, per graph, from k x nseg
  * statistics (device) of thresholds p/q (HOST, as given to tec_sweep_stats):
  *   TEC_RULE_LARGEST_JUMP: visiting the thresholds in decreasing order, the
  *     one just above the largest increase of the largest component (the
@@ -305,7 +305,7 @@ tec_status tec_oriented_csr(tec_graph *g, int64_t *ooff_out, int32_t *ocol_out);
 
 /* ---------------------------------------------------------------- learned threshold picker */
 
-/* The paper picks the threshold delta by rules of thumb (Sec. IV-E: the jump
+/* The paper picks the threshold delta by rules of thumb (Sec. IV-D: the jump
  * of the largest component, else maximum modularity).  The picker replaces
  * them with a small network trained on sweeps: inputs are the tec_features
  * rows, the output y approximates b/64 for the best grid threshold b/128 (the
@@ -363,7 +363,7 @@ tec_status tec_picker_train(tec_picker *p, const float *feats, const float *targ
  * work already queued on the picker's stream, and before the picker's next
  * use).  p_out, q_out: device, nseg int64 each (one without segments), ready
  * for tec_prune_components_batch.  Runs tec_support if needed.  The paper
- * picks thresholds by rules of thumb (Sec. IV-E); this call replaces them. */
+ * picks thresholds by rules of thumb (Sec. IV-D); this call replaces them. */
 tec_status tec_pick_threshold(tec_graph *g, tec_picker *p, const int64_t *seg_off, int nseg, int bf16,
                               int64_t *p_out, int64_t *q_out);
 

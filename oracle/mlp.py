@@ -3,7 +3,7 @@
 Float64 numpy statement of the network the CUDA picker trains: 66 inputs ->
 128 (ReLU) -> 128 (ReLU) -> 1 output, loss = mean squared error, Adam
 (Kingma & Ba 2015) with bias correction.  The paper has no learned picker
-(it chooses thresholds by rules of thumb, Sec. IV-E); the architecture is the
+(it chooses thresholds by rules of thumb, Sec. IV-D); the architecture is the
 project's.  Parameter vector layout: W1 [128 x 66] row-major, b1 [128],
 W2 [128 x 128], b2 [128], w3 [128], b3 [1].
 

@@ -335,7 +335,7 @@ def features(off, eu, ev, t):
 
 
 def sweep_stats(off, col, measure: int, ps, qs, labels, nthreads: int = 1):
-    """Per threshold p_i/q_i, the statistics Sec. IV-E plots against the
+    """Per threshold p_i/q_i, the statistics Sec. IV-D plots against the
     threshold (Fig. 6), for the labeling labels[i] of that threshold:
     ncomp (components), kept (edges with sim >= p_i/q_i), largest (size of the
     largest component), intra (edges of the input graph inside one component)
@@ -372,7 +372,7 @@ def _ascending(ps, qs):
 
 
 def rule_largest_jump(ps, qs, largest):
-    """Rule of thumb R1 (Sec. IV-E): visit the thresholds in decreasing order
+    """Rule of thumb R1 (Sec. IV-D): visit the thresholds in decreasing order
     and stop at the sudden increase of the largest component: the index of the
     threshold just above the largest increase (the highest such threshold on
     ties), or None when the largest component never grows."""
@@ -386,7 +386,7 @@ def rule_largest_jump(ps, qs, largest):
 
 
 def rule_modularity(ps, qs, modularity):
-    """Rule of thumb R2 (Sec. IV-E): the threshold of largest modularity (the
+    """Rule of thumb R2 (Sec. IV-D): the threshold of largest modularity (the
     lowest such threshold on ties)."""
     order = _ascending(ps, qs)
     best = order[0]

@@ -1,4 +1,4 @@
-// Sweep statistics and the threshold rules of thumb (Sec. IV-E, Fig. 6).
+// Sweep statistics and the threshold rules of thumb (Sec. IV-D, Fig. 6).
 //
 // For k labelings of a batch of graphs (rows of a sweep over thresholds
 // theta_r = p[r]/q[r]) and every graph s of the batch:

@@ -431,7 +431,7 @@ def stats_numpy(buf, k: int, nseg: int = 1):
 
 
 def rule_of_thumb(stats_buf, ps, qs, nseg: int = 1, rule: int = RULE_LARGEST_JUMP, stream=None):
-    """Row picked per graph by a threshold rule of thumb (Sec. IV-E): CUDA int32 tensor."""
+    """Row picked per graph by a threshold rule of thumb (Sec. IV-D): CUDA int32 tensor."""
     torch = _require_cuda()
     k = len(ps)
     hp = np.ascontiguousarray(ps, dtype=np.int64)

@@ -165,3 +165,24 @@ def test_precision_recall_f1_against_oracle(tec):
             assert abs(got[L, gi, 0] - ref[0]) <= 1e-15
             assert np.allclose(got[L, gi, 1:], ref[1:], rtol=1e-12, atol=0), (gi, L)
     g.free()
+
+
+def test_theorem1_demo(tec):
+    """The Theorem 1 / Fig. 2 demo on the GPU: TW recovers the two planted
+    blocks (mean F1 at its best threshold above 0.99) while Tectonic, K3 and
+    K4 do not reach 0.8 at any threshold; the demo's mean scores equal the
+    oracle's on the same graphs."""
+    from paper_2412_12382_gb300 import demo_theorem1 as D
+    res = D.run(seeds=6)
+    assert res["TW"]["best_mean_f1"] > 0.99
+    for name in ("Tectonic", "K3", "K4"):
+        assert res[name]["best_mean_f1"] < 0.8
+    grids = D.grids()
+    for name in ("TW", "K4"):
+        measure, ps, qs = grids[name]
+        ari = np.zeros(len(ps))
+        for s in range(6):
+            off, col, blk = sbm_csr(D.SIZES, D.PROBS, seed=100 + s)
+            lab, _ = O.sweep(off, col, measure, ps, qs)
+            ari += np.array([O.ari(lab[i], blk) for i in range(len(ps))])
+        assert np.allclose(np.array(res[name]["mean_ari"]), ari / 6, rtol=0, atol=1e-15)

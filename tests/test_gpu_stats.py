@@ -1,4 +1,4 @@
-"""Sweep statistics and the threshold rules of thumb (Sec. IV-E) on the GPU
+"""Sweep statistics and the threshold rules of thumb (Sec. IV-D) on the GPU
 against the oracle.  Integer statistics are compared exactly; modularity is
 a ratio of exact integers rounded on both sides, compared to 2e-16 absolute
 plus one part in 10^15."""

@@ -1,4 +1,4 @@
-"""Pins of the oracle's sweep statistics and rules of thumb (Sec. IV-E, Fig. 6)."""
+"""Pins of the oracle's sweep statistics and rules of thumb (Sec. IV-D, Fig. 6)."""
 import itertools
 from fractions import Fraction
 

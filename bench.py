@@ -331,6 +331,24 @@ def bench_picker(reps=3):
     return out
 
 
+def slowest(seconds: float, dist=None, device=None) -> float:
+    """The largest of every rank's `seconds` (the local value without a process group)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, seconds: float, world: int, dist=None, device=None):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank: all units over the slowest rank's time.  Returns
+    (units per second, that time)."""
+    s = slowest(seconds, dist, device)
+    return world * units_per_rank / s, s
+
+
 def run_reference(args, spec, rank, world):
     import numpy as np
     import torch
@@ -457,14 +475,10 @@ def main():
     launches = T.launch_count() - l0
     g.sync()
     stage_ms = [[e[i].elapsed_time(e[i + 1]) for e in step_ev] for i in range(4)]
-    total_ms = start.elapsed_time(end)
+    value, step_s = job_throughput(m, start.elapsed_time(end) / 1e3 / args.steps, world, dist, dev)
     if dist is not None:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
         dist.barrier()
-    ms_per_step = total_ms / args.steps
-    value = world * m / (ms_per_step / 1e3)
+    ms_per_step = step_s * 1e3
     _, ncomp = g.full_pass(TECTONIC, p, q, labels=labels, count=True)
     g.set_stage_events([])
 
@@ -491,12 +505,8 @@ def main():
         t1 = time.perf_counter()
         for _ in range(k_e2e):
             g.full_pass_host(on, cn, TECTONIC, p, q, ln)
-        e2e_s = (time.perf_counter() - t1) / k_e2e
-        if dist is not None:
-            tt = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
-        e2e = {"value": world * m / e2e_s, "unit": UNIT, "h2d_bytes_per_step": (n + 1) * 8 + nnz * 4,
+        e2e_value, _ = job_throughput(m, (time.perf_counter() - t1) / k_e2e, world, dist, dev)
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (n + 1) * 8 + nnz * 4,
                "d2h_bytes_per_step": n * 4 + 8 * 16}
         ok = np.array_equal(ln, labels.cpu().numpy())
         if not ok:

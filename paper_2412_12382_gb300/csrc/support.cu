@@ -293,6 +293,7 @@ __device__ __forceinline__ void probe_step(int32_t w, int64_t k, int slot, int32
 
 // Membership policy of the hashed staging: filter test, queue, directory.
 struct FilterSet {
+    static constexpr int ROW_LOADS = UNROLL;   // ids per lane in flight along a long row
     Staged S;
     __device__ __forceinline__ void probe(int32_t w, int64_t k, int slot, int32_t cval, uint32_t *t,
                                           WarpScratch &ws, int &qn) const {
@@ -328,7 +329,12 @@ struct CoreScratch {
     int64_t jpos[32];      // V-mode: position of c in the candidate's row
 };
 
+// Ids per lane in flight along a long row of a core visit: the bitmap test
+// is short, so more loads per lane are needed to cover memory latency.
+constexpr int C_ROW_LOADS = 16;
+
 struct CoreSet {
+    static constexpr int ROW_LOADS = C_ROW_LOADS;
     const unsigned long long *bm;   // C_WORDS words, members of the staged chunk
     const uint16_t *pref;           // per word holding members: position of its first member
     uint32_t *cnt;                  // per position: triangles on c -> member
@@ -388,15 +394,16 @@ __device__ __forceinline__ void process_batch(const int64_t *off, const int32_t 
         }
         const int64_t rs = __shfl_sync(FULL, cd.rs, src);
         const int len = __shfl_sync(FULL, cd.len, src);
-        for (int base = 0; base < len; base += 32 * UNROLL) {
-            int32_t w[UNROLL];
+        constexpr int LOADS = Set::ROW_LOADS;
+        for (int base = 0; base < len; base += 32 * LOADS) {
+            int32_t w[LOADS];
 #pragma unroll
-            for (int j = 0; j < UNROLL; ++j) {   // all loads issued before any is used
+            for (int j = 0; j < LOADS; ++j) {    // all loads issued before any is used
                 const int i = base + 32 * j + (int)lane;
                 w[j] = i < len ? __ldg(&pv[rs + i]) : -1;
             }
 #pragma unroll
-            for (int j = 0; j < UNROLL; ++j) S.probe(w[j], rs + base + 32 * j + (int)lane, src, cval, t, ws, qn);
+            for (int j = 0; j < LOADS; ++j) S.probe(w[j], rs + base + 32 * j + (int)lane, src, cval, t, ws, qn);
         }
     }
     // short rows, packed end to end

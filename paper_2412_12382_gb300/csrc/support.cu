@@ -166,7 +166,6 @@ __device__ __forceinline__ Cand load_cand(const int64_t *off, const int32_t *col
 // scan.
 
 constexpr int QCAP = 64;                 // per-warp queue of filter positives
-constexpr int PF_DEPTH = 2;              // long probe rows pulled into L2 ahead of the warp's loads
 constexpr int UNROLL = 4;                // ids loaded per lane before the first is probed
 constexpr int SHORT_ROW = 96;            // rows up to this length are packed across lanes
 
@@ -294,6 +293,7 @@ __device__ __forceinline__ void probe_step(int32_t w, int64_t k, int slot, int32
 // Membership policy of the hashed staging: filter test, queue, directory.
 struct FilterSet {
     static constexpr int ROW_LOADS = UNROLL;   // ids per lane in flight along a long row
+    static constexpr int PF_AHEAD = 2;         // long rows pulled into L2 this many rows ahead
     Staged S;
     __device__ __forceinline__ void probe(int32_t w, int64_t k, int slot, int32_t cval, uint32_t *t,
                                           WarpScratch &ws, int &qn) const {
@@ -330,11 +330,14 @@ struct CoreScratch {
 };
 
 // Ids per lane in flight along a long row of a core visit: the bitmap test
-// is short, so more loads per lane are needed to cover memory latency.
+// is short, so more loads per lane are needed to cover memory latency.  With
+// that many in flight, prefetching rows ahead costs; one bulk prefetch of
+// the row about to be read still pays (measured on R-MAT scale 26).
 constexpr int C_ROW_LOADS = 16;
 
 struct CoreSet {
     static constexpr int ROW_LOADS = C_ROW_LOADS;
+    static constexpr int PF_AHEAD = 0;
     const unsigned long long *bm;   // C_WORDS words, members of the staged chunk
     const uint16_t *pref;           // per word holding members: position of its first member
     uint32_t *cnt;                  // per position: triangles on c -> member
@@ -376,14 +379,16 @@ __device__ __forceinline__ void process_batch(const int64_t *off, const int32_t 
     ws.jpos[lane] = cd.jpos;
     __syncwarp();
     int qn = 0;
-    // long rows, one after another; the first PF_DEPTH are pulled into L2 now
-    // and each row started pulls the one PF_DEPTH rows later
+    // long rows, one after another; the first PF_AHEAD are pulled into L2 now
+    // and each row started pulls the one PF_AHEAD rows later (with PF_AHEAD
+    // = 0, itself: one bulk request for the row the warp is about to read)
     unsigned todo = __ballot_sync(FULL, cd.len > SHORT_ROW);
     unsigned pf = todo;
     {
+        constexpr int AHEAD = Set::PF_AHEAD;
         const unsigned rank = __popc(todo & ((1u << lane) - 1u));
-        if (((todo >> lane) & 1u) && rank < PF_DEPTH) l2_prefetch_ids(pv, cd.rs, cd.len);
-        for (int i = 0; i < PF_DEPTH && pf; ++i) pf &= pf - 1;
+        if (((todo >> lane) & 1u) && rank < AHEAD) l2_prefetch_ids(pv, cd.rs, cd.len);
+        for (int i = 0; i < AHEAD && pf; ++i) pf &= pf - 1;
     }
     while (todo) {
         const int src = __ffs(todo) - 1;

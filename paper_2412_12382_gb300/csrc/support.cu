@@ -47,6 +47,7 @@ constexpr int64_t VISIT_PROBES_W = 1 << 20;     // target probes per warp visit
 // hold many batches per warp for that tail to stay small.
 constexpr int64_t VISIT_PROBES_B = 1 << 25;
 constexpr int W_GRAB = 16;                      // warp visits taken per counter bump
+constexpr int64_t CORE_MIN_WORK = 1 << 16;      // probes (about) for a small core centre to get a block visit
 // Candidates per batch of a block visit.  A visit ends at a block barrier, and
 // one batch of long rows can hold many times the average batch's probes, so
 // batches smaller than a warp keep the barrier tail short.
@@ -65,15 +66,18 @@ __device__ __forceinline__ int64_t lower_bound_g(const int32_t *a, int64_t lo, i
     return lo;
 }
 
-// Candidates of one visit: du + deg candidates split into slices of vlen.
-__device__ __forceinline__ int64_t visit_len(int64_t du) {
-    int64_t v = (du <= W_MAX ? VISIT_PROBES_W : VISIT_PROBES_B) / (du > 0 ? du : 1);
+// Candidates of one visit: du + deg candidates split into slices of vlen
+// (block = a visit run by a whole block: the hashed block visits and all
+// core visits).
+__device__ __forceinline__ int64_t visit_len(int64_t du, bool block) {
+    int64_t v = (block ? VISIT_PROBES_B : VISIT_PROBES_W) / (du > 0 ? du : 1);
     return v < 256 ? 256 : (v > 65536 ? 65536 : v);
 }
 
 // One thread per vertex: emits the visits of centre c: the warp list from the
-// front of tasks[], the block list from its back, and block visits of core
-// centres (core_of[c] >= 0, when core_of is given) to ctasks[].
+// front of tasks[], the block list from its back, and the visits of core
+// centres (core_of[c] >= 0, when core_of is given) to ctasks[]: all with
+// d+(c) > W_MAX, and smaller ones with at least CORE_MIN_WORK probes.
 __global__ void k_make_visits(const int64_t *off, const int64_t *ooff, int64_t n, uint64_t *tasks, int64_t cap,
                               const int32_t *core_of, uint64_t *ctasks, unsigned long long *ctr) {
     if (graph_bad(ctr)) return;
@@ -86,12 +90,15 @@ __global__ void k_make_visits(const int64_t *off, const int64_t *ooff, int64_t n
         if (c < n) {
             du = ooff[c + 1] - ooff[c];
             deg = off[c + 1] - off[c];
-            core = core_of && du > W_MAX && core_of[c] >= 0;
+            core = core_of && core_of[c] >= 0;
         }
         // V-mode candidates exist only if c has in-neighbours
         const int64_t ncand = du > 0 ? du + (deg > du ? deg : 0) : 0;
-        const int64_t cnt = ncand > 0 ? ceil_div(ncand, visit_len(du)) : 0;
-        const bool small = du <= W_MAX;
+        // a core centre with little work stays a warp visit: a block visit
+        // costs a few block barriers however small it is
+        if (core && du <= W_MAX && ncand * du < CORE_MIN_WORK) core = false;
+        const bool small = du <= W_MAX && !core;
+        const int64_t cnt = ncand > 0 ? ceil_div(ncand, visit_len(du, !small)) : 0;
         const int64_t my_w = small ? cnt : 0, my_b = (small || core) ? 0 : cnt, my_c = core ? cnt : 0;
         int64_t sw = my_w, sb = my_b, sc = my_c;   // inclusive warp scans
 #pragma unroll
@@ -481,7 +488,7 @@ __device__ __forceinline__ void warp_visit(const int64_t *off, const int32_t *co
     const int du = (int)(ooff[c + 1] - cb);
     const int64_t deg = off[c + 1] - off[c];
     const int64_t ncand = du + (deg > du ? deg : 0);
-    const int64_t vl = visit_len(du);
+    const int64_t vl = visit_len(du, false);
     const int64_t qbeg = vis * vl, qend = min(ncand, qbeg + vl);
     Staged S{s_a, du, s_cnt, filt, filter_bits(du, W_FB), dir, 0, 0, 0};
     for (int i = (int)lane; i < (1 << S.fb) / 32; i += 32) filt[i] = 0u;
@@ -542,7 +549,7 @@ k_support(const int64_t *off, const int32_t *col, const uint32_t *flags, const i
         const int64_t du = ooff[c + 1] - cb;
         const int64_t deg = off[c + 1] - off[c];
         const int64_t ncand = du + (deg > du ? deg : 0);
-        const int64_t vl = visit_len(du);
+        const int64_t vl = visit_len(du, true);
         const int64_t qbeg = vis * vl, qend = min(ncand, qbeg + vl);
         const bool chunked = du > S_CHUNK;
         for (int64_t c0 = 0; c0 < du; c0 += S_CHUNK) {
@@ -714,7 +721,7 @@ k_support_core(const int64_t *off, const int32_t *col, const uint32_t *flags, co
         const int64_t du = ooff[c + 1] - cb;
         const int64_t deg = off[c + 1] - off[c];
         const int64_t ncand = du + (deg > du ? deg : 0);
-        const int64_t vl = visit_len(du);
+        const int64_t vl = visit_len(du, true);
         const int64_t qbeg = vis * vl, qend = min(ncand, qbeg + vl);
         const bool chunked = du > C_CHUNK;
         const int32_t cval = core_of[c];

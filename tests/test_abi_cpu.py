@@ -51,6 +51,19 @@ def test_null_arguments_rejected_without_touching_a_device(lib):
     assert L.tec_graph_info(None, None, None) == 1          # TEC_EINVAL
     assert L.tec_prune(None, 0, 1, 10, None, None) == 1
     assert L.tec_graph_create(-1, 0, None, None) == 1
+    # the later entry points check their arguments before any device call
+    assert L.tec_sweep(None, 0, None, None, 64, None, 0, None, None) == 1
+    assert L.tec_sweep_stats(None, 0, None, None, 64, None, None, 0, None) == 1
+    assert L.tec_rule_of_thumb(None, None, None, 0, 1, 0, None, None) == 1       # k < 1
+    assert L.tec_rule_of_thumb(None, None, None, 200, 1, 0, None, None) == 1     # k > 127
+    assert L.tec_edge_k4(None, None) == 1
+    assert L.tec_prf(None, 1, None, None, None, 0, None) == 1
+    assert L.tec_ari(None, 1, None, None, None, 0, None) == 1
+    assert L.tec_features(None, None, 0, None) == 1
+    assert L.tec_pick_threshold(None, None, None, 0, 1, None, None) == 1
+    assert L.tec_set_core_staging(None, 1) == 1
+    assert L.tec_prune_components_batch(None, 0, None, None, None, 0, None, None) == 1
+    assert L.tec_picker_thresholds(None, -1, None, None, None) == 1
 
 
 def test_binding_fails_loudly_without_gpu():

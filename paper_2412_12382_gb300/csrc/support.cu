@@ -17,18 +17,24 @@
 //
 // The candidates of centre c are indexed 0 .. d+(c) + deg(c) - 1: first the
 // U-mode candidates N+(c), then the entries of c's symmetric row (V-mode).  A
-// visit is a contiguous slice of them, sized for about 2^20 probes:
-//   d+(c) <= 256  warp visits: N+(c) staged in the warp's own slice of shared
-//                 memory (sorted ids, bitmap filter, bucket directory);
-//   d+(c) >  256  block visits: N+(c) staged per block in chunks of 4096 ids
-//                 (sorted ids, bitmap filter, bucket directory); the block's
-//                 warps take batches of candidates from a shared counter.
-// A warp handles 32 candidates at once: each lane loads one candidate's row
-// bounds (one round of latency for 32 rows); long rows are then read one after
-// another by the whole warp, coalesced, 128 ids per step, and short rows are
-// packed end to end over the lanes.  One persistent kernel (two blocks per SM)
-// drains the block visits first, pulling them from a global counter, then
-// reuses the same shared memory for warp visits.
+// visit is a contiguous slice of them, sized by probes:
+//   core visits   centres of degree >= D (a core of at most 2^20 vertices, see
+//                 "core staging" below) with enough work: N+(c) staged per
+//                 block as an exact bitmap over core codes, 2^25 probes;
+//   warp visits   other centres with d+(c) <= 256: N+(c) staged in the warp's
+//                 own slice of shared memory (sorted ids, bitmap filter,
+//                 bucket directory), 2^20 probes;
+//   block visits  the rest: N+(c) staged per block in chunks of 4096 ids
+//                 (sorted ids, bitmap filter, bucket directory), 2^25 probes.
+// In a block or core visit the block's warps take batches of 8 candidates
+// from a shared counter; a warp visit walks its candidates 32 at a time.  Each
+// lane loads one candidate's row bounds (one round of latency per batch); long
+// rows are then read one after another by the whole warp, coalesced, with 4
+// (hashed staging) or 16 (core staging) ids per lane in flight, and short
+// rows are packed end to end over the lanes.  Two persistent kernels: one
+// 1024-thread block per SM for the core visits, then two 512-thread blocks per
+// SM that drain the block visits and reuse the same shared memory for warp
+// visits.
 #include <climits>
 
 #include "tec_internal.cuh"
@@ -42,8 +48,8 @@ constexpr int B_THREADS = 512;                  // block-visit kernel block
 constexpr int B_WARPS = B_THREADS / 32;
 constexpr int S_CHUNK = 4096;                   // staged ids per block chunk
 constexpr int64_t VISIT_PROBES_W = 1 << 20;     // target probes per warp visit
-// Target probes per block visit.  A block visit ends at a block barrier, so
-// its warps idle for up to one 32-candidate batch at the end: the visit must
+// Target probes per block (and core) visit.  A block visit ends at a block
+// barrier, so its warps idle for up to one batch at the end: the visit must
 // hold many batches per warp for that tail to stay small.
 constexpr int64_t VISIT_PROBES_B = 1 << 25;
 constexpr int W_GRAB = 16;                      // warp visits taken per counter bump

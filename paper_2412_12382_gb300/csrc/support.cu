@@ -58,6 +58,7 @@ constexpr int64_t CORE_MIN_WORK = 1 << 16;      // probes (about) for a small co
 // one batch of long rows can hold many times the average batch's probes, so
 // batches smaller than a warp keep the barrier tail short.
 constexpr int B_BATCH = 8;
+constexpr int C_BATCH = 8;                      // the same for core visits
 constexpr uint64_t VIS_MASK = (1ull << 32) - 1;
 
 __device__ __forceinline__ bool out_bit(const uint32_t *flags, int64_t e) {
@@ -306,6 +307,7 @@ __device__ __forceinline__ void probe_step(int32_t w, int64_t k, int slot, int32
 // Membership policy of the hashed staging: filter test, queue, directory.
 struct FilterSet {
     static constexpr int ROW_LOADS = UNROLL;   // ids per lane in flight along a long row
+    static constexpr int SHORT_LOADS = UNROLL; // ids per lane in flight over packed short rows
     static constexpr int PF_AHEAD = 2;         // long rows pulled into L2 this many rows ahead
     Staged S;
     __device__ __forceinline__ void probe(int32_t w, int64_t k, int slot, int32_t cval, uint32_t *t,
@@ -347,9 +349,11 @@ struct CoreScratch {
 // that many in flight, prefetching rows ahead costs; one bulk prefetch of
 // the row about to be read still pays (measured on R-MAT scale 26).
 constexpr int C_ROW_LOADS = 16;
+constexpr int C_SHORT_LOADS = 4;
 
 struct CoreSet {
     static constexpr int ROW_LOADS = C_ROW_LOADS;
+    static constexpr int SHORT_LOADS = C_SHORT_LOADS;
     static constexpr int PF_AHEAD = 0;
     const unsigned long long *bm;   // C_WORDS words, members of the staged chunk
     const uint16_t *pref;           // per word holding members: position of its first member
@@ -434,12 +438,13 @@ __device__ __forceinline__ void process_batch(const int64_t *off, const int32_t 
     }
     const int sstart = incl - slen;
     const int stotal = __shfl_sync(FULL, incl, 31);
-    for (int e0 = 0; e0 < stotal; e0 += 32 * UNROLL) {
-        int32_t w[UNROLL];
-        int64_t kk[UNROLL];
-        int own[UNROLL];
+    constexpr int SLOADS = Set::SHORT_LOADS;
+    for (int e0 = 0; e0 < stotal; e0 += 32 * SLOADS) {
+        int32_t w[SLOADS];
+        int64_t kk[SLOADS];
+        int own[SLOADS];
 #pragma unroll
-        for (int j = 0; j < UNROLL; ++j) {
+        for (int j = 0; j < SLOADS; ++j) {
             const int e = e0 + 32 * j + (int)lane;
             int p = 0;                           // last lane whose row starts at or before e
 #pragma unroll
@@ -454,7 +459,7 @@ __device__ __forceinline__ void process_batch(const int64_t *off, const int32_t 
             w[j] = e < stotal ? __ldg(&pv[kk[j]]) : -1;
         }
 #pragma unroll
-        for (int j = 0; j < UNROLL; ++j) S.probe(w[j], kk[j], own[j], cval, t, ws, qn);
+        for (int j = 0; j < SLOADS; ++j) S.probe(w[j], kk[j], own[j], cval, t, ws, qn);
     }
     __syncwarp();
     S.finish(t, ws, qn);
@@ -750,11 +755,11 @@ k_support_core(const int64_t *off, const int32_t *col, const uint32_t *flags, co
             const int32_t lo_id = ocol[cb + c0], hi_id = ocol[cb + c0 + cl - 1];
             for (;;) {
                 int b = 0;
-                if (lane == 0) b = atomicAdd(&s_next, B_BATCH);
+                if (lane == 0) b = atomicAdd(&s_next, C_BATCH);
                 b = __shfl_sync(FULL, b, 0);
                 if (qbeg + b >= qend) break;
                 process_batch(off, col, flags, ooff, ocol, pv2, t, c, cval, cb, du, qbeg + b,
-                              min(qend, qbeg + b + B_BATCH), chunked, lo_id, hi_id, S, s_cnt, false, ws, ctr);
+                              min(qend, qbeg + b + C_BATCH), chunked, lo_id, hi_id, S, s_cnt, false, ws, ctr);
             }
             __syncthreads();
             for (int i = threadIdx.x; i < cl; i += C_THREADS) {

@@ -446,7 +446,6 @@ __global__ void k_prf_final(const unsigned long long *sums, const int64_t *seg_o
     out[3 * i] = nv > 0 ? (double)sums[3 * i] / (double)nv : 0.0;
     out[3 * i + 1] = __longlong_as_double((long long)sums[3 * i + 1]) * inv;
     out[3 * i + 2] = __longlong_as_double((long long)sums[3 * i + 2]) * inv;
-    (void)inv;
 }
 
 __device__ double i128_to_double(__int128 v) {

@@ -375,6 +375,36 @@ def test_precision_recall_f1():
     assert (p, r) == (0.5, 1.0) and abs(f - 2 / 3) < 1e-15
 
 
+def test_precision_recall_f1_hand_worked():
+    """Sec. IV-A on a hand-worked case.  Truth blocks {0..3}, {4,5}, {6,7};
+    found {0,1,2}, {3,4,5,6}, {7}.  Matches by Jaccard: {0,1,2} -> block 0
+    (3/4; p 1, r 3/4), {3,4,5,6} -> block 1 (2/4 beats 1/7 and 1/5; p 1/2,
+    r 1), {7} -> block 2 (1/2; p 1, r 1/2).  Size-weighted over 8 vertices:
+    P = 6/8, R = 27/32, F1 = (3 * 6/7 + 4 * 2/3 + 1 * 2/3) / 8 = 31/42."""
+    truth = np.array([0, 0, 0, 0, 1, 1, 2, 2])
+    found = np.array([5, 5, 5, 1, 1, 1, 1, 9])
+    p, r, f = O.precision_recall_f1(truth, found)
+    assert p == 0.75 and r == 27 / 32 and abs(f - 31 / 42) < 1e-15
+    # labels are names only: renaming either side changes nothing
+    assert O.precision_recall_f1(truth + 7, 100 - found) == (p, r, f)
+
+
+def test_precision_recall_f1_jaccard_tie():
+    """A Jaccard tie between truth blocks of different sizes: found {0,1,2}
+    meets block 0 = {0} in 1 (Jaccard 1/3) and block 1 = {1..5} in 2 (2/6 =
+    1/3).  The lower block id wins (p 1/3, r 1); block 1 would give p 2/3,
+    r 2/5.  Vertices 3, 4, 5 form a found community matched to block 1 (3/5;
+    p 1, r 3/5)."""
+    truth = np.array([0, 1, 1, 1, 1, 1])
+    found = np.array([0, 0, 0, 1, 1, 1])
+    p, r, f = O.precision_recall_f1(truth, found)
+    assert abs(p - (3 * (1 / 3) + 3 * 1) / 6) < 1e-15
+    assert abs(r - (3 * 1 + 3 * (3 / 5)) / 6) < 1e-15
+    f_tie = 2 * (1 / 3) / (4 / 3)
+    f_rest = 2 * (3 / 5) / (8 / 5)
+    assert abs(f - (3 * f_tie + 3 * f_rest) / 6) < 1e-15
+
+
 def test_features_shape_and_normalisation():
     off, col = small.two_cliques_bridge(6, 9)
     eu, ev = O.edge_list(off, col)

@@ -3,6 +3,7 @@ import itertools
 from fractions import Fraction
 
 import numpy as np
+import pytest
 
 import oracle as O
 from graphgen import csr_from_pairs, small
@@ -76,3 +77,25 @@ def test_no_jump_falls_back_to_modularity():
     assert all(s["largest"] == 1 and s["kept"] == 0 for s in stats)
     assert O.rule_largest_jump(GRID_P, GRID_Q, [s["largest"] for s in stats]) is None
     assert O.rule_of_thumb(GRID_P, GRID_Q, stats) == 0      # all modularities equal: the lowest threshold
+
+
+def test_modularity_against_networkx():
+    """Newman-Girvan modularity of the sweep's levels and of arbitrary
+    labelings, against networkx's implementation of the same definition."""
+    nx = pytest.importorskip("networkx")
+    nxc = pytest.importorskip("networkx.algorithms.community")
+    rng = np.random.default_rng(11)
+    off, col = small.gnp(60, 0.12, rng)
+    n = len(off) - 1
+    eu, ev = O.edge_list(off, col)
+    G = nx.Graph()
+    G.add_nodes_from(range(n))
+    G.add_edges_from(zip(eu.tolist(), ev.tolist()))
+    labels, _ = O.sweep(off, col, O.TECTONIC, GRID_P, GRID_Q)
+    cases = [labels[i] for i in (0, 8, 20, 63)] + [rng.integers(0, k, n) for k in (2, 5)]
+    stats = O.sweep_stats(off, col, O.TECTONIC, [1] * len(cases), [128] * len(cases), cases)
+    for lab, st in zip(cases, stats):
+        parts = {}
+        for x in range(n):
+            parts.setdefault(int(lab[x]), set()).add(x)
+        assert abs(st["modularity"] - nxc.modularity(G, list(parts.values()))) <= 1e-12

@@ -43,7 +43,7 @@ WORKLOADS = {
 # DRAM bytes per launch of the triangle-count stage from an ncu capture, per
 # unit of algorithmic bytes, valid only for the support.cu it was taken on
 # (see profiles/).  None until a capture exists for the current source.
-TRAFFIC_CAPTURE = {"support_sha": "09d352078cee0069", "dram_per_alg_byte": 86.645 / 49.162954,
+TRAFFIC_CAPTURE = {"support_sha": "cbc4243a25e3c702", "dram_per_alg_byte": 86.630 / 49.162954,
                    "source": "ncu DRAM bytes of the triangle-count stage's kernels at R-MAT scale 22, "
                              "scaled by algorithmic bytes"}
 

@@ -58,7 +58,7 @@ constexpr int64_t CORE_MIN_WORK = 1 << 16;      // probes (about) for a small co
 // one batch of long rows can hold many times the average batch's probes, so
 // batches smaller than a warp keep the barrier tail short.
 constexpr int B_BATCH = 8;
-constexpr int C_BATCH = 8;                      // the same for core visits
+constexpr int C_BATCH = 16;                     // candidates per batch in core visits (bitmap tests are short)
 constexpr uint64_t VIS_MASK = (1ull << 32) - 1;
 
 __device__ __forceinline__ bool out_bit(const uint32_t *flags, int64_t e) {

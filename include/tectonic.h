@@ -52,7 +52,8 @@ typedef enum tec_status {
     TEC_ECUDA = 3,      /* a CUDA runtime call failed; the message names it */
     TEC_ETIMEOUT = 4,   /* a bounded device loop hit its cap; the graph stays usable */
     TEC_EOVERFLOW = 5,  /* a size or threshold does not fit the checked integer width */
-    TEC_EBADGRAPH = 6,  /* validation found an unsorted row, self-loop, duplicate or asymmetry */
+    TEC_EBADGRAPH = 6,  /* validation found an unsorted row, self-loop, duplicate or asymmetry,
+                           or a label or block id was out of range */
     TEC_ESTATE = 7      /* a call needs a step that has not been run (e.g. components before prune) */
 } tec_status;
 
@@ -194,9 +195,11 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
 tec_status tec_features(tec_graph *g, const int64_t *seg_off, int nseg, float *feat_out);
 
 /* Adjusted Rand index (Hubert & Arabie 1985) between k labelings (device,
- * k x n int32, e.g. the output of tec_sweep, labels relative to each graph
- * when seg_off is given) and reference blocks truth (device, n int32, block
- * ids 0..63 within each graph; TEC_EBADGRAPH at the next wait otherwise).
+ * k x n int32, e.g. the output of tec_sweep: each label is a vertex id of its
+ * graph, 0 <= label < that graph's vertex count, relative to the graph's first
+ * vertex when seg_off is given) and reference blocks truth (device, n int32,
+ * block ids 0..63 within each graph).  A vertex whose label or block id is
+ * out of range is skipped and TEC_EBADGRAPH is reported at the next wait.
  * ari_out: device, k x nseg float64 (k values without segments).  Pair counts
  * are exact integers; the final ratio has a relative error below 1e-15.  The
  * paper evaluates with matched precision / recall (Sec. IV-A); ARI is the

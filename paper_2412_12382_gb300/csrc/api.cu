@@ -85,7 +85,8 @@ tec_status read_counters(tec_graph *g) {
         TEC_CUDA(cudaStreamSynchronize(g->stream));
         if (st & ST_BADGRAPH) {
             g->oriented = g->supported = g->pruned = g->hooked = false;
-            return set_error(TEC_EBADGRAPH, "the CSR is not a simple undirected graph with sorted rows");
+            return set_error(TEC_EBADGRAPH, "invalid input on the device: a CSR that is not a simple undirected graph "
+                                            "with sorted rows, or a label or block id out of range");
         }
         g->pruned = g->hooked = false;
         return set_error(TEC_ETIMEOUT, "a bounded device loop reached its iteration cap");

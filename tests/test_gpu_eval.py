@@ -171,9 +171,10 @@ def test_precision_recall_f1_hand_worked(tec):
     """The hand-worked Sec. IV-A cases of the oracle pins, on the GPU: sizes
     4/2/2 against found 3/4/1 (P 3/4, R 27/32, F1 31/42), and a Jaccard tie
     between a block of 1 and a block of 5 that must go to the lower block id
-    (P 4/6, R 4/5; the other choice would give P 5/6)."""
+    (P 4/6, R 4/5; the other choice would give P 5/6).  Labels are vertex
+    ids of the graph; one out of range is skipped and reported."""
     import torch
-    cases = [(np.array([0, 0, 0, 0, 1, 1, 2, 2]), np.array([5, 5, 5, 1, 1, 1, 1, 9]), (0.75, 27 / 32, 31 / 42)),
+    cases = [(np.array([0, 0, 0, 0, 1, 1, 2, 2]), np.array([5, 5, 5, 1, 1, 1, 1, 7]), (0.75, 27 / 32, 31 / 42)),
              (np.array([0, 1, 1, 1, 1, 1]), np.array([0, 0, 0, 1, 1, 1]),
               (4 / 6, 0.8, (3 * 0.5 + 3 * 0.75) / 6))]
     for truth, found, (p, r, f) in cases:
@@ -182,7 +183,18 @@ def test_precision_recall_f1_hand_worked(tec):
         got = g.prf(torch.from_numpy(found.astype(np.int32)[None, :]).cuda(),
                     torch.from_numpy(truth.astype(np.int32)).cuda()).cpu().numpy()[0, 0]
         assert got[0] == p and abs(got[1] - r) <= 1e-15 and abs(got[2] - f) <= 1e-15, got
+        g.sync()
         g.free()
+    # label 8 on an 8-vertex graph: vertex 7 is left out (P 5/8) and the next wait reports it
+    off, col = small.cycle(8)
+    g = _graph(tec, off, col)
+    got = g.prf(torch.tensor([[5, 5, 5, 1, 1, 1, 1, 8]], dtype=torch.int32, device="cuda"),
+                torch.tensor([0, 0, 0, 0, 1, 1, 2, 2], dtype=torch.int32, device="cuda")).cpu().numpy()[0, 0]
+    assert got[0] == 5 / 8
+    with pytest.raises(tec.TectonicError) as e:
+        g.sync()
+    assert e.value.status == 6
+    g.free()
 
 
 def test_theorem1_demo(tec):

@@ -1,6 +1,7 @@
 // C ABI entry points (include/tectonic.h): argument checks, graph memory,
 // step ordering and status reporting.  All device work is in the kernels of
-// orient.cu, support.cu, prune.cu, cc.cu and scan.cu.
+// the other .cu files (orientation, triangle counts, K4, pruning, components,
+// sweep, statistics, evaluation, picker).
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -258,6 +259,21 @@ std::vector<int> ascending_rows(const int64_t *p, const int64_t *q, int k) {
     return order;
 }
 
+// Size counters and the level-tagged cell table shared by tec_ari and tec_prf.
+// Each buffer is allocated on its own, so one whose allocation failed is
+// retried by the next call; a fresh buffer, or a new vertex count (counters
+// beyond the old n may be stale), forces the zeroing of all three.
+tec_status ensure_cell_tables(tec_graph *g, int64_t tsize) {
+    const int64_t ncap = std::max<int64_t>(g->n_cap, 1);
+    if (!g->ari_size || !g->ari_keys || !g->ari_cnt) g->ari_tag = ~0ull;
+    if (!g->ari_size) TEC_TRY(dalloc(&g->ari_size, 2 * ncap, "component sizes"));
+    if (!g->ari_keys) TEC_TRY(dalloc(&g->ari_keys, tsize, "cell keys"));
+    if (!g->ari_cnt) TEC_TRY(dalloc(&g->ari_cnt, tsize, "cell counts"));
+    if (g->ari_n != g->n) g->ari_tag = ~0ull;
+    g->ari_n = g->n;
+    return TEC_OK;
+}
+
 template <class T>
 tec_status grow(T **buf, int64_t *cap, int64_t need, const char *what) {
     if (*cap >= need) return TEC_OK;
@@ -299,14 +315,7 @@ tec_status tec_ari(tec_graph *g, int k, const int32_t *labels, const int32_t *tr
     const int ns = seg_off ? nseg : 1;
     TEC_TRY(ensure_seg_scratch(g, ns));
     const int64_t tsize = (int64_t)1 << ari_table_bits(g->n_cap);
-    if (!g->ari_size) {
-        TEC_TRY(dalloc(&g->ari_size, 2 * std::max<int64_t>(g->n_cap, 1), "component sizes"));
-        TEC_TRY(dalloc(&g->ari_keys, tsize, "cell keys"));
-        TEC_TRY(dalloc(&g->ari_cnt, tsize, "cell counts"));
-        g->ari_tag = ~0ull;                      // forces the first zeroing
-    }
-    if (g->ari_n != g->n) g->ari_tag = ~0ull;   // size counters beyond the old n may be stale
-    g->ari_n = g->n;
+    TEC_TRY(ensure_cell_tables(g, tsize));
     TEC_CUDA(launch_ari(labels, k, truth, g->n, seg_off, nseg, g->seg_hist, g->ari_size, std::max<int64_t>(g->n_cap, 1),
                         g->ari_keys, g->ari_cnt, tsize, g->ari_sums, ari_out, &g->ari_tag, g->ctr, g->stream));
     return TEC_OK;
@@ -325,17 +334,10 @@ tec_status tec_prf(tec_graph *g, int k, const int32_t *labels, const int32_t *tr
     TEC_TRY(ensure_seg_scratch(g, ns));
     const int64_t tsize = (int64_t)1 << ari_table_bits(g->n_cap);
     const int64_t ncap = std::max<int64_t>(g->n_cap, 1);
-    if (!g->ari_size) {
-        TEC_TRY(dalloc(&g->ari_size, 2 * ncap, "component sizes"));
-        TEC_TRY(dalloc(&g->ari_keys, tsize, "cell keys"));
-        TEC_TRY(dalloc(&g->ari_cnt, tsize, "cell counts"));
-        g->ari_tag = ~0ull;
-    }
     if (!g->prf_best) TEC_TRY(dalloc(&g->prf_best, ncap, "best matches"));
     if (!g->prf_bestb) TEC_TRY(dalloc(&g->prf_bestb, ncap, "matched blocks"));
     TEC_TRY(grow(&g->prf_sums, &g->prf_sums_cap, (int64_t)3 * ns * ARI_CHUNK, "P/R/F1 sums"));
-    if (g->ari_n != g->n) g->ari_tag = ~0ull;
-    g->ari_n = g->n;
+    TEC_TRY(ensure_cell_tables(g, tsize));
     TEC_CUDA(launch_prf(labels, k, truth, g->n, seg_off, nseg, g->seg_hist, g->ari_size, ncap, g->ari_keys, g->ari_cnt,
                         tsize, g->ari_sums, g->prf_best, g->prf_bestb, g->prf_sums, prf_out, &g->ari_tag, g->ctr,
                         g->stream));
@@ -686,11 +688,7 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
     }
     DeviceGuard dg(g->device);
     const int nsl = seg_off ? nseg : 1;
-    // thresholds in ascending value, equal values kept in input order
-    std::vector<int> order(k);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return (__int128)p[a] * q[b] < (__int128)p[b] * q[a]; });
+    const std::vector<int> order = ascending_rows(p, q, k);
     std::vector<int64_t> hthr(2 * k);
     for (int i = 0; i < k; ++i) {
         hthr[i] = p[order[i]];

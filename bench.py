@@ -551,7 +551,7 @@ def main():
                        "l2": f"inputs larger than L2: CSR {nnz * 4 / 1e9:.2f} GB vs 0.129 GB",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "pass_alg_bytes": ab["B_alg_min"], "pass_alg_GBps": pass_gbs,
-                       "pass_alg_bytes_survey_W": ab["B_alg"],
+                       "pass_alg_bytes_W": ab["B_alg"],
                        "pass_frac_of_peak": pass_gbs / peak,
                        "stage_ms": {"orient": statistics.mean(stage_ms[0]), "support": sup_ms,
                                     "prune_hook": statistics.mean(stage_ms[2]),

@@ -203,7 +203,7 @@ tec_status tec_features(tec_graph *g, const int64_t *seg_off, int nseg, float *f
  * ari_out: device, k x nseg float64 (k values without segments).  Pair counts
  * are exact integers; the final ratio has a relative error below 1e-15.  The
  * paper evaluates with matched precision / recall (Sec. IV-A); ARI is the
- * project's judge of the picker. */
+ * score this project trains and rates the picker by. */
 tec_status tec_ari(tec_graph *g, int k, const int32_t *labels, const int32_t *truth, const int64_t *seg_off, int nseg,
                    double *ari_out);
 

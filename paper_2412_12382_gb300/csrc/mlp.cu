@@ -1,7 +1,8 @@
 // Learned threshold picker: a 66 -> 128 -> 128 -> 1 ReLU network on the
 // per-graph features of tec_features, trained with mean squared error and
 // Adam (Kingma & Ba 2015).  The paper picks thresholds by rules of thumb
-// (Sec. IV-D); this network replaces them and the full sweep judges it.
+// (Sec. IV-D); this network replaces them, rated against the best threshold
+// of the full sweep.
 //
 // Parameters (float32, one device vector): W1 [128 x 66] row-major, b1 [128],
 // W2 [128 x 128], b2 [128], w3 [128], b3.  A step on a batch of B samples:

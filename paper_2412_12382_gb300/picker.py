@@ -98,11 +98,20 @@ def save(picker, path, meta=None):
              meta=json.dumps(meta or {}), sha256=digest)
 
 
-def load(path):
+def read_checkpoint(path):
+    """The arrays of a checkpoint written by `save`, after checking the sha256
+    of parameters and Adam moments (host only; ValueError on a mismatch)."""
     d = np.load(path, allow_pickle=False)
     params, m, v = d["params"], d["adam_m"], d["adam_v"]
+    if params.shape != (T.PICKER_PARAMS,) or m.shape != params.shape or v.shape != params.shape:
+        raise ValueError(f"checkpoint {path} does not hold {T.PICKER_PARAMS} parameters and moments")
     if hashlib.sha256(params.tobytes() + m.tobytes() + v.tobytes()).hexdigest() != str(d["sha256"]):
         raise ValueError(f"checkpoint {path} fails its checksum")
+    return params, m, v, int(d["step"]), json.loads(str(d["meta"]))
+
+
+def load(path):
+    params, m, v, step, meta = read_checkpoint(path)
     picker = T.Picker(params)
-    picker.set_params(params, m, v, int(d["step"]))
-    return picker, json.loads(str(d["meta"]))
+    picker.set_params(params, m, v, step)
+    return picker, meta

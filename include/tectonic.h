@@ -149,9 +149,12 @@ tec_status tec_edge_k4(tec_graph *g, uint32_t *k4_out);
 tec_status tec_edge_weights(tec_graph *g, tec_measure measure, double *w_out);
 
 /* Algorithm 1, first step: keeps edge e iff sim(e) >= p/q, i.e. removes
- * exactly the edges with sim(e) < delta.  Decided in exact integer arithmetic:
- * Tectonic: t*q >= p*(deg u + deg v); TW: (3t + 2 - deg u - deg v)*q >= p.
- * q must be > 0 (TEC_EINVAL); |p| and q must be < 2^62 (TEC_EOVERFLOW).
+ * exactly the edges with sim(e) < delta.  Decided in exact integer arithmetic
+ * (64-bit products when |p|, q < 2^28, 128-bit otherwise):
+ *   Tectonic: t*q >= p*(deg u + deg v);   TW: (3t + 2 - deg u - deg v)*q >= p;
+ *   Jaccard:  t*q >= p*(deg u + deg v - t);   K3: t*q >= p;   K4: K4(e)*q >= p.
+ * q must be > 0 (TEC_EINVAL); |p| and q must be < 2^62, and a K4 threshold
+ * at most 2^32 - 1 (TEC_EOVERFLOW).
  * keep_out (device, m bytes, canonical order) may be NULL; kept_out (HOST,
  * may be NULL; waits when given) receives the number of kept edges.  The mask
  * stays on the device for tec_components. */
@@ -285,6 +288,8 @@ tec_status tec_full_pass_host(tec_graph *g, const int64_t *row_off_host, const i
  * codes in id order, and a copy of the oriented columns holds those codes
  * (4 bytes per edge).  Centres of degree >= D then stage their out-rows as
  * exact bitmaps over the codes: no false positives and no positive queue.
+ * (A centre with an out-row of at most 256 ids takes this path only with
+ * about 2^16 probes or more; below that it keeps the hashed warp visit.)
  * Disabling it frees no memory but skips the copy and stages every centre by
  * hashing; the counts are identical either way.  The next call that needs the
  * triangle counts recomputes them. */
@@ -312,10 +317,11 @@ tec_status tec_oriented_csr(tec_graph *g, int64_t *ooff_out, int32_t *ocol_out);
  * of the largest component, else maximum modularity).  The picker replaces
  * them with a small network trained on sweeps: inputs are the tec_features
  * rows, the output y approximates b/64 for the best grid threshold b/128 (the
- * one of highest ARI), and the prediction is b = clamp(round(64 y), 1, 64).  Network: 66 -> 128 (ReLU) -> 128 (ReLU) -> 1,
- * float32 parameters in one vector: W1 [128 x 66] row-major, b1 [128],
- * W2 [128 x 128], b2 [128], w3 [128], b3.  Loss: mean squared error.
- * Optimiser: Adam with bias correction. */
+ * one of highest ARI), and the prediction is b = clamp(round(64 y), 1, 64).
+ * Network: 66 -> 128 (ReLU) -> 128 (ReLU) -> 1, float32 parameters in one
+ * vector: W1 [128 x 66] row-major, b1 [128], W2 [128 x 128], b2 [128],
+ * w3 [128], b3.  Loss: mean squared error.  Optimiser: Adam with bias
+ * correction. */
 #define TEC_PICKER_INPUTS 66
 #define TEC_PICKER_HIDDEN 128
 #define TEC_PICKER_PARAMS 25217

@@ -3,6 +3,8 @@ public header declares, and the binding refuses to run without a GPU."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -73,3 +75,20 @@ def test_binding_fails_loudly_without_gpu():
     from paper_2412_12382_gb300 import Graph
     with pytest.raises(RuntimeError):
         Graph(n_cap=4, nnz_cap=8)
+
+
+def test_c_client_compiles_links_and_runs(lib, tmp_path):
+    """The header is plain C11 (-pedantic -Werror) and a C program linked
+    against the library gets the documented statuses without a device."""
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(libbuild.library_path())
+    exe = str(tmp_path / "abi_smoke")
+    src = os.path.join(ROOT, "tests", "abi_c", "abi_smoke.c")
+    cmd = [gcc, "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+           src, "-o", exe, "-L", libdir, "-ltectonic", f"-Wl,-rpath,{libdir}"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr

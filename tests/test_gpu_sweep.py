@@ -56,6 +56,22 @@ def test_sweep_rmat_and_random(tec):
     check_sweep(tec, off, col, O.TECTONIC, GRID[::3] + [(0, 1), (1, 2)])
 
 
+def test_sweep_127_thresholds_wide_and_equal_values(tec):
+    """The largest k (127) in shuffled order, with 63 grid values b/128 also
+    given as (b 2^33)/(128 2^33): equal values in another representation, and
+    numerators and denominators past 2^28, so every edge level comes from
+    128-bit comparisons."""
+    rng = np.random.default_rng(12)
+    th = GRID + [(b << 33, 128 << 33) for b in range(1, 64)]
+    assert len(th) == 127
+    th = [th[i] for i in rng.permutation(len(th))]
+    off, col, _ = planted_partition(4, 200, 0.25, 0.01, seed=4)      # levels from 1 to 800 components
+    check_sweep(tec, off, col, O.TECTONIC, th)
+    tw = [(d << 35, 1 << 35) for d in range(-40, 10)] + [(d, 1) for d in range(-40, 10)]
+    off, col, _ = sbm_csr([50, 50], [[0.1, 0.05], [0.05, 0.8]], seed=5)
+    check_sweep(tec, off, col, O.TW, [tw[i] for i in rng.permutation(len(tw))])
+
+
 def test_sweep_degenerate(tec):
     for off, col in (small.complete(12), small.star(9), small.empty(4), small.two_cliques_bridge(5, 6)):
         check_sweep(tec, off, col, O.TECTONIC, [(0, 1), (1, 1000), (5, 12), (1, 2), (1, 1)])

@@ -235,9 +235,11 @@ typedef struct tec_sweep_stat {
 
 /* Statistics of k labelings (device, k x n int32, labels relative to each
  * graph when seg_off is given, row i the components at p[i]/q[i]: the output
- * of tec_sweep, or of tec_prune_components_batch at those thresholds).  The
- * labelings must be nested as a sweep's are (a lower threshold never splits
- * a component); `intra` is found by binary search over them.  p, q: HOST,
+ * of tec_sweep, or of tec_prune_components_batch at those thresholds).  Each
+ * label must be the smallest vertex id of its component, as those calls
+ * write it: components are counted at the vertices labelled by themselves.
+ * The labelings must be nested as a sweep's are (a lower threshold never
+ * splits a component); `intra` is found by binary search over them.  p, q: HOST,
  * k <= 127, q > 0.  stats_out: device, k x nseg (row-major by threshold).
  * Per-graph edge counts must stay below 2^31.  Runs tec_support if needed. */
 tec_status tec_sweep_stats(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q, int k,

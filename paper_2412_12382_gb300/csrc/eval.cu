@@ -1,4 +1,5 @@
-// Per-graph features for the threshold picker and the adjusted Rand index.
+// Per-graph features for the threshold picker, the adjusted Rand index, and
+// precision / recall / F1 (Sec. IV-A) of labelings against planted blocks.
 //
 // Features (tec_features): the 64-bin histogram of Tectonic weights on the
 // grid i/128 -- bin = min(63, floor(128 t / (deg u + deg v))), the level an

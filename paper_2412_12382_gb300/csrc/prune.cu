@@ -2,9 +2,11 @@
 //
 // Tectonic (Table 1) keeps oriented edge u->v iff t*q >= p*(deg u + deg v);
 // TW (Eq. 1) keeps it iff (3t + 2 - deg u - deg v)*q >= p, since
-// wedge = |N(u) u N(v)| - t - 2 = deg u + deg v - 2t - 2.  Algorithm 1 removes
-// only edges with sim < p/q, so equality keeps the edge.  Products fit int64
-// when |p|, q < 2^28; larger thresholds take the 128-bit path.
+// wedge = |N(u) u N(v)| - t - 2 = deg u + deg v - 2t - 2; Jaccard iff
+// t*q >= p*(deg u + deg v - t); K3 iff t*q >= p; K4 is the K3 test on the
+// 4-clique counts (keep_edge in tec_internal.cuh).  Algorithm 1 removes only
+// edges with sim < p/q, so equality keeps the edge.  Products fit int64 when
+// |p|, q < 2^28; larger thresholds take the 128-bit path.
 //
 // The prune kernel streams the oriented edges in tiles of 2048, finds each
 // edge's source row by binary search in the tile's row range, writes one keep

@@ -174,7 +174,13 @@ class Graph:
     """A graph resident on the GPU (a ``tec_graph``).
 
     ``off`` / ``col``: symmetric CSR, either CUDA tensors (int64 or int32
-    offsets, int32 ids) or numpy arrays (copied from host memory)."""
+    offsets, int32 ids) or numpy arrays (copied from host memory).
+
+    Every call runs on the graph's stream (``stream``, by default torch's
+    current stream when the graph is made), and output tensors are allocated
+    by torch on the current stream.  Use the graph from that stream, or
+    synchronise before touching its results (or, for CUDA input tensors,
+    before freeing them) from another one."""
 
     def __init__(self, off=None, col=None, *, n_cap: int | None = None, nnz_cap: int | None = None,
                  validate: bool = False, stream=None):

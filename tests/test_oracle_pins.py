@@ -415,6 +415,13 @@ def test_features_shape_and_normalisation():
     assert abs(f[:64].sum() - 1.0) < 1e-15
     assert f[64] == math.log(2 * m / n) and f[65] == math.log(m)
     assert f[0] == 1 / m                       # the bridge has t = 0
+    # by hand: K6 edges have t = 4, K9 edges t = 7; an edge at a bridge end
+    # has one more degree.  K6: 10 edges at 4/10 -> bin 51, 5 at 4/11 -> 46;
+    # K9: 28 edges at 7/16 -> bin 56, 8 at 7/17 -> 52; bridge: bin 0.
+    expect = {0: 1, 46: 5, 51: 10, 52: 8, 56: 28}
+    assert m == 52 and n == 15
+    for b in range(64):
+        assert f[b] == expect.get(b, 0) / m, b
 
 
 # ----------------------------------------------------------- paper statistics

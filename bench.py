@@ -6,9 +6,14 @@ theta = 1/10 with fused union-find hooking, component labels.  Default
 workload: R-MAT scale 26, edge factor 32, (a,b,c,d) = (0.57,0.19,0.19,0.05),
 seed 3, generated on the GPU (untimed input preparation).
 
-Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
-bounded edge sample instead.  Under torchrun every rank runs its own replica
-(the path does not shard: replicas only) and rank 0 reports the total.
+Prints one JSON line (rank 0): the pass's edges/s, the triangle stage
+against the measured HBM bandwidth (`roofline`), the same pass from host
+buffers (`e2e`), the oracle on a bounded sample (`cpu_baseline`), and two
+further blocks: the batched 64-threshold sweep over 256 DC-SBM graphs and
+the learned picker against the full sweep on 500 held-out DC-SBM graphs.
+`--impl reference` times the CPU oracle on a bounded edge sample instead.
+Under torchrun every rank runs its own replica (the path does not shard:
+replicas only) and rank 0 reports the total.
 """
 from __future__ import annotations
 

@@ -25,12 +25,19 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA library cannot be built")
 
 
-def library_path() -> str:
+def default_library_path() -> str:
+    """The in-tree build that build() writes."""
     return os.path.join(BUILD, "libtectonic.so")
 
 
-def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+def library_path() -> str:
+    """The library the binding loads: $TEC_LIBRARY when set (a variant built
+    by the autotuner), else the in-tree build."""
+    return os.environ.get("TEC_LIBRARY") or default_library_path()
+
+
+def _sources(csrc: str = CSRC):
+    return sorted(glob.glob(os.path.join(csrc, "*.cu")))
 
 
 def _deps():
@@ -39,22 +46,22 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    lib = library_path()
+    lib = default_library_path()
     if not os.path.exists(lib):
         return False
     t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and up_to_date():
-        return library_path()
-    os.makedirs(BUILD, exist_ok=True)
+def compile_library(csrc: str, build_dir: str, ptxas_info: bool = False):
+    """Compiles every .cu of `csrc` in parallel and links build_dir/libtectonic.so.
+    Returns (library path, {source name: compiler diagnostics})."""
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+        obj = os.path.join(build_dir, os.path.basename(src).replace(".cu", ".o"))
         cmd = [cc] + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -62,18 +69,26 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return obj, r.stderr
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        results = list(ex.map(compile_one, _sources()))
-    if verbose or ptxas_info:
-        for obj, err in results:
-            if err.strip():
-                print(f"--- {os.path.basename(obj)}\n{err}")
-    tmp = library_path() + f".tmp{os.getpid()}"
+        results = list(ex.map(compile_one, _sources(csrc)))
+    lib = os.path.join(build_dir, "libtectonic.so")
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in results] + ARCH
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, library_path())
-    return library_path()
+    os.replace(tmp, lib)
+    return lib, {os.path.basename(o).replace(".o", ".cu"): err for o, err in results}
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+    if not force and up_to_date():
+        return default_library_path()
+    lib, diags = compile_library(CSRC, BUILD, ptxas_info)
+    if verbose or ptxas_info:
+        for name, err in diags.items():
+            if err.strip():
+                print(f"--- {name}\n{err}")
+    return lib
 
 
 if __name__ == "__main__":

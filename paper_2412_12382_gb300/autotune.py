@@ -8,7 +8,9 @@ the current values are built first as that baseline) is rejected, and so is
 one that fails to build.  Each kept variant is timed by running a command,
 normally a short ``bench.py`` run, with ``TEC_LIBRARY`` pointing the binding
 at the variant's library.  A metric is read from the command's last JSON
-line, and the median of ``reps`` runs is the variant's cost.
+line, and the median of ``reps`` runs is the variant's cost.  A check
+command (``--check-cmd``, e.g. the GPU parity tests) can be required to pass
+against each variant before it is timed.
 
 The search is coordinate descent from the current values: each parameter in
 turn takes its best candidate with the others fixed, until a full round
@@ -51,6 +53,8 @@ TUNABLES = {
     "VISIT_PROBES_B": ("support.cu", [1 << 23, 1 << 24, 1 << 25, 1 << 26]),
     "W_GRAB": ("support.cu", [4, 8, 16, 32]),
     "K4_GRAB": ("k4.cu", [1, 2, 4, 8]),
+    "VCHUNK_V": ("tec_internal.cuh", [4, 8, 16]),      # vertices per lane in the sweep's vertex passes
+    "BS_CHUNK": ("eval.cu", [2048, 4096, 8192, 16384]),
 }
 
 
@@ -194,13 +198,20 @@ def coordinate_descent(space: dict, start: dict, evaluate, lower_is_better: bool
     return best, best_cost, seen
 
 
-def tune(params, cmd, metric, reps=3, lower_is_better=True, cache_path=None, device="", cwd=None, log=print):
+def check_variant(lib: str, check_cmd: str, cwd: str) -> bool:
+    """Runs a correctness command (e.g. the GPU parity tests) against the variant."""
+    env = dict(os.environ, TEC_LIBRARY=lib)
+    return subprocess.run(shlex.split(check_cmd), capture_output=True, text=True, env=env, cwd=cwd).returncode == 0
+
+
+def tune(params, cmd, metric, reps=3, lower_is_better=True, cache_path=None, device="", cwd=None, log=print,
+         check_cmd=None):
     cwd = cwd or os.path.dirname(HERE)
     texts = {f: open(os.path.join(_build.CSRC, f)).read() for f in {TUNABLES[p][0] for p in params}}
     start = {p: int_value(current_value(texts[TUNABLES[p][0]], p)) for p in params}
     space = {p: sorted(set(TUNABLES[p][1]) | {start[p]}) for p in params}
     key = json.dumps({"device": device, "sources": source_hash(), "cmd": cmd, "metric": metric,
-                      "reps": reps})
+                      "reps": reps, "check": check_cmd})
     cache = {}
     if cache_path and os.path.exists(cache_path):
         cache = json.load(open(cache_path))
@@ -224,6 +235,9 @@ def tune(params, cmd, metric, reps=3, lower_is_better=True, cache_path=None, dev
             if bad:
                 log(f"{point}: spills more than the current sources in {', '.join(bad)}, skipped")
                 entries[pk] = None
+            elif check_cmd and not check_variant(lib, check_cmd, cwd):
+                log(f"{point}: fails the check command, skipped")
+                entries[pk] = None
             else:
                 entries[pk] = time_variant(lib, cmd, metric, reps, cwd)
                 log(f"{point}: {entries[pk]:.4g}")
@@ -242,6 +256,9 @@ def main(argv=None):
     ap.add_argument("--cmd", required=True, help="timing command, run from the repository root")
     ap.add_argument("--metric", required=True, help="dotted path of the value in the command's JSON line")
     ap.add_argument("--higher-is-better", action="store_true")
+    ap.add_argument("--check-cmd", default=None,
+                    help="correctness command each variant must pass before it is timed, e.g. "
+                         "'python -m pytest tests/test_gpu_parity.py -m gpu -x -q'")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--cache", default="autotune_cache.json")
     args = ap.parse_args(argv)
@@ -254,7 +271,7 @@ def main(argv=None):
     except ImportError:
         pass
     start, best, cost, _ = tune(params, args.cmd, args.metric, args.reps, not args.higher_is_better,
-                                args.cache, device)
+                                args.cache, device, check_cmd=args.check_cmd)
     print(json.dumps({"start": start, "best": best, "cost": cost, "metric": args.metric}))
     return 0
 

@@ -100,6 +100,15 @@ def test_a_variant_builds_with_nvcc(tmp_path):
     assert A.int_value(A.current_value(open(os.path.join(B.CSRC, "support.cu")).read(), "C_BATCH")) != 12
 
 
+def test_a_variant_failing_its_check_is_not_timed(tmp_path, monkeypatch):
+    monkeypatch.setattr(A, "build_variant", lambda point, root: ("lib.so", {}))
+    monkeypatch.setattr(A, "check_variant", lambda lib, cmd, cwd: False)
+    timed = []
+    monkeypatch.setattr(A, "time_variant", lambda *a: timed.append(a) or 1.0)
+    start, best, cost, entries = A.tune(["K4_GRAB"], "cmd", "m", reps=1, log=lambda *a: None, check_cmd="check")
+    assert timed == [] and cost is None and all(v is None for v in entries.values())
+
+
 def test_library_override_is_only_for_loading(monkeypatch):
     monkeypatch.setenv("TEC_LIBRARY", "/nonexistent/variant.so")
     assert B.library_path() == "/nonexistent/variant.so"

@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import hashlib
 import json
+import os
 
 import numpy as np
 
@@ -43,6 +44,63 @@ def build_dataset(seeds, n_lo=1000, n_hi=100000, batch=256, measure=T.TECTONIC):
     out = {k: torch.cat([p[k] for p in parts], dim=1 if k == "ari" else 0) for k in ("feats", "best", "best_ari", "ari")}
     out["target"] = (out["best"].to(torch.float32) + 1.0) / K
     return out
+
+
+DATASET_FIELDS = ("feats", "best", "best_ari", "ari", "target")
+
+
+def dataset_key(seeds, n_lo, n_hi, measure=T.TECTONIC) -> str:
+    """Identity of a labelled dataset: its seeds, size range, measure and grid
+    (the labels are exact, so the kernels' version does not enter)."""
+    desc = json.dumps({"seeds": [int(x) for x in seeds], "n": [int(n_lo), int(n_hi)], "measure": int(measure),
+                       "grid": [K, DEN]})
+    return hashlib.sha256(desc.encode()).hexdigest()[:16]
+
+
+def _dataset_digest(arrays) -> str:
+    h = hashlib.sha256()
+    for name in DATASET_FIELDS:
+        h.update(name.encode())
+        h.update(np.ascontiguousarray(arrays[name]).tobytes())
+    return h.hexdigest()
+
+
+def save_dataset(dataset, path, key: str):
+    """Writes a dataset (tensors on any device) with its key and a checksum."""
+    arrays = {name: dataset[name].detach().cpu().numpy() for name in DATASET_FIELDS}
+    np.savez(path, key=key, sha256=_dataset_digest(arrays), **arrays)
+
+
+def load_dataset(path, key: str, device="cuda"):
+    """The dataset saved at `path` as torch tensors on `device`, or None when
+    the file is missing or was saved under another key.  ValueError when the
+    arrays fail their checksum."""
+    import torch
+    if not os.path.exists(path):
+        return None
+    d = np.load(path, allow_pickle=False)
+    if str(d["key"]) != key:
+        return None
+    arrays = {name: d[name] for name in DATASET_FIELDS}
+    if _dataset_digest(arrays) != str(d["sha256"]):
+        raise ValueError(f"dataset {path} fails its checksum")
+    return {name: torch.from_numpy(arrays[name]).to(device) for name in DATASET_FIELDS}
+
+
+def cached_dataset(seeds, n_lo=1000, n_hi=100000, cache_dir=None, batch=256, measure=T.TECTONIC,
+                   device="cuda"):
+    """build_dataset, kept under cache_dir (when given) as dataset_<key>.npz
+    and reused by later runs with the same seeds, size range and measure."""
+    if not cache_dir:
+        return build_dataset(seeds, n_lo, n_hi, batch, measure)
+    key = dataset_key(seeds, n_lo, n_hi, measure)
+    path = os.path.join(cache_dir, f"dataset_{key}.npz")
+    ds = load_dataset(path, key, device)
+    if ds is None:
+        ds = build_dataset(seeds, n_lo, n_hi, batch, measure)
+        os.makedirs(cache_dir, exist_ok=True)
+        save_dataset(ds, path, key)
+    return ds
 
 
 def fixed_level(dataset) -> int:

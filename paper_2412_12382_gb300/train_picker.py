@@ -38,15 +38,17 @@ def main(argv=None):
     ap.add_argument("--train-seeds", type=int, nargs=2, default=(10000, 20000))
     ap.add_argument("--eval-seeds", type=int, nargs=2, default=(20000, 20500))
     ap.add_argument("--n-range", type=int, nargs=2, default=(1000, 100000))
+    ap.add_argument("--dataset-cache", default=None,
+                    help="directory for the labelled datasets (features + best levels), reused by later runs")
     args = ap.parse_args(argv)
     build.build()
     t0 = time.time()
     seeds = list(range(*args.train_seeds))
     val_seeds = seeds[::10]
     tr_seeds = [s for s in seeds if s % 10 != seeds[0] % 10]
-    train = P.build_dataset(tr_seeds, *args.n_range)
-    val = P.build_dataset(val_seeds, *args.n_range)
-    held = P.build_dataset(list(range(*args.eval_seeds)), *args.n_range)
+    train = P.cached_dataset(tr_seeds, *args.n_range, cache_dir=args.dataset_cache)
+    val = P.cached_dataset(val_seeds, *args.n_range, cache_dir=args.dataset_cache)
+    held = P.cached_dataset(list(range(*args.eval_seeds)), *args.n_range, cache_dir=args.dataset_cache)
     t_data = time.time() - t0
     pk = P.T.Picker(P.init_params(0))
     best = (float("inf"), None, 0)

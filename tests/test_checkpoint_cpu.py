@@ -1,6 +1,8 @@
-"""Picker checkpoints on the host: the shipped weights pass their checksum and
-carry the training record; a file whose parameters, moments or size were
-changed after saving is refused before anything reaches a device."""
+"""Picker checkpoints and cached training sets on the host: the shipped
+weights pass their checksum and carry the training record; a file whose
+parameters, moments or size were changed after saving is refused before
+anything reaches a device; a cached dataset round-trips, is keyed by its
+seeds and size range, and fails loudly when altered."""
 import json
 import os
 
@@ -61,3 +63,49 @@ def test_round_trip_of_a_new_checkpoint(tmp_path):
     assert np.array_equal(p2, params) and np.array_equal(m2, m) and np.array_equal(v2, v)
     assert step == 17 and meta == {"epochs": 3}
     assert json.loads(str(np.load(path)["meta"])) == {"epochs": 3}
+
+
+def _fake_dataset(torch, seed=0, graphs=7):
+    g = torch.Generator().manual_seed(seed)
+    best = torch.randint(0, 64, (graphs,), generator=g)
+    return {"feats": torch.rand((graphs, 66), generator=g), "best": best,
+            "best_ari": torch.rand((graphs,), generator=g, dtype=torch.float64),
+            "ari": torch.rand((64, graphs), generator=g, dtype=torch.float64),
+            "target": (best.to(torch.float32) + 1.0) / 64}
+
+
+def test_dataset_cache_round_trip_key_and_checksum(tmp_path):
+    torch = pytest.importorskip("torch")
+    ds = _fake_dataset(torch)
+    key = P.dataset_key(range(10000, 10007), 1000, 100000)
+    assert key != P.dataset_key(range(10000, 10008), 1000, 100000)       # other seeds, other key
+    assert key != P.dataset_key(range(10000, 10007), 1000, 200000)
+    path = str(tmp_path / "ds.npz")
+    P.save_dataset(ds, path, key)
+    back = P.load_dataset(path, key, device="cpu")
+    for name in P.DATASET_FIELDS:
+        assert torch.equal(back[name], ds[name]), name
+    assert P.load_dataset(path, "another key", device="cpu") is None
+    assert P.load_dataset(str(tmp_path / "missing.npz"), key, device="cpu") is None
+    d = dict(np.load(path, allow_pickle=False))
+    d["best_ari"] = d["best_ari"].copy()
+    d["best_ari"][3] += 1e-12
+    np.savez(path, **d)
+    with pytest.raises(ValueError, match="checksum"):
+        P.load_dataset(path, key, device="cpu")
+
+
+def test_cached_dataset_builds_once(tmp_path, monkeypatch):
+    torch = pytest.importorskip("torch")
+    calls = []
+
+    def fake_build(seeds, n_lo, n_hi, batch, measure):
+        calls.append(list(seeds))
+        return _fake_dataset(torch, seed=len(calls))
+
+    monkeypatch.setattr(P, "build_dataset", fake_build)
+    a = P.cached_dataset([1, 2, 3], cache_dir=str(tmp_path), device="cpu")
+    b = P.cached_dataset([1, 2, 3], cache_dir=str(tmp_path), device="cpu")
+    assert len(calls) == 1 and torch.equal(a["feats"], b["feats"])
+    P.cached_dataset([1, 2, 4], cache_dir=str(tmp_path), device="cpu")
+    assert len(calls) == 2

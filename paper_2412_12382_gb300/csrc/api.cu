@@ -11,9 +11,22 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "tec_internal.cuh"
 
 namespace tec {
+
+// Names the host-side span of an entry point for profilers (Nsight can then
+// select the kernels one call launched).  Without a tool attached NVTX calls
+// return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define TEC_RANGE() ::tec::NvtxRange tec_nvtx_range_(__func__)
 
 static thread_local char g_err[1024];
 
@@ -291,6 +304,7 @@ extern "C" {
 
 tec_status tec_features(tec_graph *g, const int64_t *seg_off, int nseg, float *feat_out) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     if (!feat_out) return set_error(TEC_EINVAL, "feat_out is NULL");
     if (seg_off && nseg < 1) return set_error(TEC_EINVAL, "nseg must be >= 1 with a segment table");
@@ -306,6 +320,7 @@ tec_status tec_features(tec_graph *g, const int64_t *seg_off, int nseg, float *f
 tec_status tec_ari(tec_graph *g, int k, const int32_t *labels, const int32_t *truth, const int64_t *seg_off, int nseg,
                    double *ari_out) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     if (k < 1) return set_error(TEC_EINVAL, "k must be >= 1");
     if ((!labels || !truth) && g->n > 0) return set_error(TEC_EINVAL, "labels or truth is NULL");
@@ -324,6 +339,7 @@ tec_status tec_ari(tec_graph *g, int k, const int32_t *labels, const int32_t *tr
 tec_status tec_prf(tec_graph *g, int k, const int32_t *labels, const int32_t *truth, const int64_t *seg_off, int nseg,
                    double *prf_out) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     if (k < 1) return set_error(TEC_EINVAL, "k must be >= 1");
     if ((!labels || !truth) && g->n > 0) return set_error(TEC_EINVAL, "labels or truth is NULL");
@@ -426,6 +442,7 @@ tec_status tec_graph_create(int64_t n_cap, int64_t nnz_cap, void *stream, tec_gr
 tec_status tec_graph_load(tec_graph *g, const void *row_off, int off_is_i64, const int32_t *col, int64_t n,
                           int64_t nnz, uint32_t flags) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     if (n < 0 || n > g->n_cap) return set_error(TEC_EINVAL, "n=%lld exceeds the capacity %lld", (long long)n, (long long)g->n_cap);
     if (nnz < 0 || nnz > g->nnz_cap) return set_error(TEC_EINVAL, "nnz=%lld exceeds the capacity %lld", (long long)nnz, (long long)g->nnz_cap);
@@ -524,6 +541,7 @@ tec_status tec_sync(tec_graph *g) {
 
 tec_status tec_orient(tec_graph *g) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     DeviceGuard dg(g->device);
     g->oriented = false;
@@ -532,6 +550,7 @@ tec_status tec_orient(tec_graph *g) {
 
 tec_status tec_support(tec_graph *g) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     DeviceGuard dg(g->device);
     g->supported = false;
@@ -563,6 +582,7 @@ tec_status tec_edge_support(tec_graph *g, uint32_t *t_out, uint32_t *wedge_out) 
 
 tec_status tec_edge_k4(tec_graph *g, uint32_t *k4_out) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     if (!k4_out && g->m > 0) return set_error(TEC_EINVAL, "k4_out is NULL");
     DeviceGuard dg(g->device);
@@ -575,6 +595,7 @@ tec_status tec_edge_k4(tec_graph *g, uint32_t *k4_out) {
 
 tec_status tec_edge_weights(tec_graph *g, tec_measure measure, double *w_out) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     if (measure < TEC_TECTONIC || measure > TEC_K4) return set_error(TEC_EINVAL, "unknown measure %d", (int)measure);
     if (!w_out && g->m > 0) return set_error(TEC_EINVAL, "w_out is NULL");
@@ -591,6 +612,7 @@ tec_status tec_edge_weights(tec_graph *g, tec_measure measure, double *w_out) {
 tec_status tec_prune(tec_graph *g, tec_measure measure, int64_t p, int64_t q, uint8_t *keep_out,
                      int64_t *kept_out) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     TEC_TRY(check_threshold((int)measure, p, q));
     DeviceGuard dg(g->device);
@@ -619,6 +641,7 @@ tec_status tec_prune(tec_graph *g, tec_measure measure, int64_t p, int64_t q, ui
 
 tec_status tec_components(tec_graph *g, int32_t *labels_out, int64_t *ncomp_out) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     if (!g->pruned) return set_error(TEC_ESTATE, "tec_components needs a tec_prune first");
     if (!labels_out && g->n > 0) return set_error(TEC_EINVAL, "labels_out is NULL");
@@ -640,6 +663,7 @@ tec_status tec_components(tec_graph *g, int32_t *labels_out, int64_t *ncomp_out)
 tec_status tec_full_pass(tec_graph *g, tec_measure measure, int64_t p, int64_t q, int32_t *labels_out,
                          int64_t *ncomp_out) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     TEC_TRY(check_threshold((int)measure, p, q));
     if (!labels_out && g->n > 0) return set_error(TEC_EINVAL, "labels_out is NULL");
@@ -656,6 +680,7 @@ tec_status tec_full_pass_host(tec_graph *g, const int64_t *row_off_host, const i
                               int64_t nnz, tec_measure measure, int64_t p, int64_t q, int32_t *labels_host,
                               int64_t *ncomp_out) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     if (!labels_host && n > 0) return set_error(TEC_EINVAL, "labels_host is NULL");
     TEC_TRY(check_threshold((int)measure, p, q));
@@ -676,6 +701,7 @@ tec_status tec_full_pass_host(tec_graph *g, const int64_t *row_off_host, const i
 tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q, int k,
                      const int64_t *seg_off, int nseg, int32_t *labels_out, int64_t *ncomp_out) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     if (k < 1 || k > 127) return set_error(TEC_EINVAL, "k must be in [1, 127] (got %d)", k);
     if (!p || !q) return set_error(TEC_EINVAL, "threshold arrays are NULL");
@@ -779,6 +805,7 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
 tec_status tec_sweep_stats(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q, int k,
                            const int32_t *labels, const int64_t *seg_off, int nseg, tec_sweep_stat *stats_out) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     if (k < 1 || k > 127) return set_error(TEC_EINVAL, "k must be in [1, 127] (got %d)", k);
     if (!p || !q || !stats_out) return set_error(TEC_EINVAL, "NULL argument");
@@ -829,6 +856,7 @@ tec_status tec_rule_of_thumb(const tec_sweep_stat *stats, const int64_t *p, cons
 tec_status tec_prune_components_batch(tec_graph *g, tec_measure measure, const int64_t *p, const int64_t *q,
                                       const int64_t *seg_off, int nseg, int32_t *labels_out, int64_t *ncomp_out) {
     clear_error();
+    TEC_RANGE();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     if (measure < TEC_TECTONIC || measure > TEC_K4) return set_error(TEC_EINVAL, "unknown measure %d", (int)measure);
     if (!p || !q || !seg_off || nseg < 1) return set_error(TEC_EINVAL, "thresholds and segment table are required");

@@ -53,12 +53,13 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def compile_library(csrc: str, build_dir: str, ptxas_info: bool = False):
+def compile_library(csrc: str, build_dir: str, ptxas_info: bool = False, defines=()):
     """Compiles every .cu of `csrc` in parallel and links build_dir/libtectonic.so.
-    Returns (library path, {source name: compiler diagnostics})."""
+    `defines`: extra preprocessor names (e.g. TEC_DEBUG).  Returns (library
+    path, {source name: compiler diagnostics})."""
     os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + [f"-D{d}" for d in defines]
 
     def compile_one(src):
         obj = os.path.join(build_dir, os.path.basename(src).replace(".cu", ".o"))
@@ -91,6 +92,20 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     return lib
 
 
+DEBUG_BUILD = os.path.join(HERE, "_build_debug")
+
+
+def build_debug() -> str:
+    """The debug library (-DTEC_DEBUG: canary bytes after every graph-owned
+    device buffer, checked by tec_sync) in _build_debug/; load it by setting
+    TEC_LIBRARY to the returned path."""
+    lib, _ = compile_library(CSRC, DEBUG_BUILD, defines=("TEC_DEBUG",))
+    return lib
+
+
 if __name__ == "__main__":
     import sys
-    print(build(force=True, verbose=True, ptxas_info="-v" in sys.argv))
+    if "--debug" in sys.argv:
+        print(build_debug())
+    else:
+        print(build(force=True, verbose=True, ptxas_info="-v" in sys.argv))

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <atomic>
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -61,11 +62,53 @@ struct DeviceGuard {
     }
 };
 
+#ifdef TEC_DEBUG
+// Debug builds (-DTEC_DEBUG): every graph-owned device buffer is followed by
+// CANARY_BYTES bytes of 0xA5, and tec_sync checks them all; a kernel that
+// wrote past the end of a buffer is reported with the buffer's name.  This
+// stands in for a memory checker where none can be run.
+constexpr size_t CANARY_BYTES = 256;
+constexpr unsigned char CANARY = 0xA5;
+struct CanaryEntry {
+    void *p;
+    size_t bytes;
+    const char *what;
+};
+std::mutex g_canary_mu;
+std::vector<CanaryEntry> g_canaries;
+
+tec_status check_canaries() {
+    TEC_CUDA(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lock(g_canary_mu);
+    std::vector<unsigned char> h(CANARY_BYTES);
+    for (const CanaryEntry &c : g_canaries) {
+        TEC_CUDA(cudaMemcpy(h.data(), (char *)c.p + c.bytes, CANARY_BYTES, cudaMemcpyDeviceToHost));
+        for (unsigned char v : h)
+            if (v != CANARY)
+                return set_error(TEC_ECUDA, "debug build: the %zu bytes after %s (%zu bytes) were overwritten",
+                                 CANARY_BYTES, c.what, c.bytes);
+    }
+    return TEC_OK;
+}
+#endif
+
 template <typename T>
 tec_status dalloc(T **p, int64_t count, const char *what) {
     *p = nullptr;
     size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+#ifdef TEC_DEBUG
+    cudaError_t e = cudaMalloc((void **)p, bytes + CANARY_BYTES);
+    if (e == cudaSuccess) e = cudaMemset((char *)*p + bytes, CANARY, CANARY_BYTES);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(g_canary_mu);
+        g_canaries.push_back({(void *)*p, bytes, what});
+    } else if (*p) {
+        cudaFree(*p);
+    }
+#else
     cudaError_t e = cudaMalloc((void **)p, bytes);
+#endif
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -73,6 +116,22 @@ tec_status dalloc(T **p, int64_t count, const char *what) {
                          "cudaMalloc of %zu bytes for %s failed: %s", bytes, what, cudaGetErrorString(e));
     }
     return TEC_OK;
+}
+
+// Frees a buffer from dalloc (NULL is ignored).
+void dfree(void *p) {
+    if (!p) return;
+#ifdef TEC_DEBUG
+    {
+        std::lock_guard<std::mutex> lock(g_canary_mu);
+        for (size_t i = 0; i < g_canaries.size(); ++i)
+            if (g_canaries[i].p == p) {
+                g_canaries.erase(g_canaries.begin() + (long)i);
+                break;
+            }
+    }
+#endif
+    cudaFree(p);
 }
 
 void free_graph_memory(tec_graph *g) {
@@ -83,8 +142,7 @@ void free_graph_memory(tec_graph *g) {
                     g->core_of, g->pv2, g->ctasks, g->core_tc, g->core_hist, g->k4, g->k4_next,
                     g->prf_best, g->prf_bestb, g->prf_sums,
                     g->st_hist, g->st_sums, g->st_cnt_n, g->st_cnt_v, g->ctr};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
+    for (void *p : ptrs) dfree(p);
     if (g->ctr_host) cudaFreeHost(g->ctr_host);
 }
 
@@ -135,8 +193,7 @@ tec_status ensure_support(tec_graph *g) {
             dalloc(&g->core_tc, 2 * tiles + 64, "core tile counts") != TEC_OK ||
             dalloc(&g->core_hist, 36, "degree histogram") != TEC_OK) {
             void *part[] = {g->core_of, g->pv2, g->ctasks, g->core_tc, g->core_hist};
-            for (void *q2 : part)
-                if (q2) cudaFree(q2);
+            for (void *q2 : part) dfree(q2);
             g->core_of = nullptr;
             g->pv2 = nullptr;
             g->ctasks = nullptr;
@@ -251,8 +308,8 @@ namespace tec {
 namespace {
 tec_status ensure_seg_scratch(tec_graph *g, int ns) {
     if (g->seg_cap >= ns) return TEC_OK;
-    if (g->seg_hist) cudaFree(g->seg_hist);
-    if (g->ari_sums) cudaFree(g->ari_sums);
+    dfree(g->seg_hist);
+    dfree(g->ari_sums);
     g->seg_hist = nullptr;
     g->ari_sums = nullptr;
     g->seg_cap = 0;
@@ -290,7 +347,7 @@ tec_status ensure_cell_tables(tec_graph *g, int64_t tsize) {
 template <class T>
 tec_status grow(T **buf, int64_t *cap, int64_t need, const char *what) {
     if (*cap >= need) return TEC_OK;
-    if (*buf) cudaFree(*buf);
+    dfree(*buf);
     *buf = nullptr;
     *cap = 0;
     TEC_TRY(dalloc(buf, need, what));
@@ -536,7 +593,12 @@ tec_status tec_sync(tec_graph *g) {
     clear_error();
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     DeviceGuard dg(g->device);
+#ifdef TEC_DEBUG
+    TEC_TRY(read_counters(g));
+    return check_canaries();
+#else
     return read_counters(g);
+#endif
 }
 
 tec_status tec_orient(tec_graph *g) {
@@ -727,7 +789,7 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
     if (!g->bucket) TEC_TRY(dalloc(&g->bucket, 3 * 127 + 4, "level buckets"));
     if (!g->thr) TEC_TRY(dalloc(&g->thr, 2 * 127, "thresholds"));
     if (g->sw_ncomp_cap < (int64_t)k * nsl) {
-        if (g->sw_ncomp) cudaFree(g->sw_ncomp);
+        dfree(g->sw_ncomp);
         g->sw_ncomp = nullptr;
         g->sw_ncomp_cap = 0;
         TEC_TRY(dalloc(&g->sw_ncomp, (int64_t)k * nsl, "component counts"));
@@ -741,8 +803,7 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
         if (dalloc(&g->msf_u, cap, "live edges") != TEC_OK || dalloc(&g->msf_v, cap, "live edges") != TEC_OK ||
             dalloc(&g->msf_k, cap, "live edge keys") != TEC_OK || dalloc(&g->msf_cnt, tiles, "live edge counts") != TEC_OK) {
             void *part[] = {g->msf_u, g->msf_v, g->msf_k, g->msf_cnt};
-            for (void *q2 : part)
-                if (q2) cudaFree(q2);
+            for (void *q2 : part) dfree(q2);
             g->msf_u = g->msf_v = g->msf_cnt = nullptr;
             g->msf_k = nullptr;
             g->msf_cap = -1;
@@ -863,7 +924,7 @@ tec_status tec_prune_components_batch(tec_graph *g, tec_measure measure, const i
     if (!labels_out && g->n > 0) return set_error(TEC_EINVAL, "labels_out is NULL");
     DeviceGuard dg(g->device);
     if (g->sw_ncomp_cap < nseg) {
-        if (g->sw_ncomp) cudaFree(g->sw_ncomp);
+        dfree(g->sw_ncomp);
         g->sw_ncomp = nullptr;
         g->sw_ncomp_cap = 0;
         TEC_TRY(dalloc(&g->sw_ncomp, nseg, "component counts"));

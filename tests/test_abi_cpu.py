@@ -92,3 +92,24 @@ def test_c_client_compiles_links_and_runs(lib, tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
+def test_debug_build_compiles_and_answers_from_c(tmp_path):
+    """The -DTEC_DEBUG library (canaries after every graph-owned buffer)
+    builds, exports the same symbols, and a C client linked to it gets the
+    same statuses without a device."""
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lib_path, _ = libbuild.compile_library(libbuild.CSRC, str(tmp_path / "dbg"), defines=("TEC_DEBUG",))
+    dbg = ctypes.CDLL(lib_path)
+    missing = [s for s in declared_symbols() if not hasattr(dbg, s)]
+    assert not missing, missing
+    exe = str(tmp_path / "abi_smoke_dbg")
+    src = os.path.join(ROOT, "tests", "abi_c", "abi_smoke.c")
+    libdir = os.path.dirname(lib_path)
+    r = subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), src, "-o", exe, "-L", libdir,
+                        "-ltectonic", f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr

@@ -3,6 +3,7 @@
 // the other .cu files (orientation, triangle counts, K4, pruning, components,
 // sweep, statistics, evaluation, picker).
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <atomic>
@@ -90,6 +91,14 @@ tec_status check_canaries() {
     }
     return TEC_OK;
 }
+
+// Failure injection: with TEC_DEBUG_FAIL_ALLOC set, every allocation whose
+// name contains that text fails as if the device were out of memory, so the
+// fallback and retry paths can be driven on purpose.
+bool injected_alloc_failure(const char *what) {
+    const char *pat = getenv("TEC_DEBUG_FAIL_ALLOC");
+    return pat && *pat && strstr(what, pat) != nullptr;
+}
 #endif
 
 template <typename T>
@@ -97,6 +106,9 @@ tec_status dalloc(T **p, int64_t count, const char *what) {
     *p = nullptr;
     size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
 #ifdef TEC_DEBUG
+    if (injected_alloc_failure(what))
+        return set_error(TEC_ENOMEM, "cudaMalloc of %zu bytes for %s failed: injected by TEC_DEBUG_FAIL_ALLOC",
+                         bytes, what);
     cudaError_t e = cudaMalloc((void **)p, bytes + CANARY_BYTES);
     if (e == cudaSuccess) e = cudaMemset((char *)*p + bytes, CANARY, CANARY_BYTES);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();

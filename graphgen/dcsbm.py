@@ -31,7 +31,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from .csr import csr_from_pairs
-from .prng import STREAM_DCSBM, draw, mix64_int, stream_key, uniform53
+from .prng import STREAM_DCSBM, draw, stream_key, uniform53
 
 M32 = np.uint64(0xFFFFFFFF)
 

@@ -400,13 +400,18 @@ tec_status tec_picker_thresholds(const float *y, int64_t N, int64_t *p_out, int6
  * (eu[e], ev[e]) given as device int32 arrays; keep (device, m bytes) selects
  * the edges to use, NULL uses all.  labels_out (device, n int32) receives the
  * smallest vertex id of each vertex's component; ncomp_out (host, may be NULL)
- * the number of components.  Runs on `stream` and waits for it; an endpoint
- * outside [0, n) gives TEC_EINVAL.
+ * the number of components.  Runs on `stream`; every call then copies a
+ * status word back to the host and waits for `stream`.  An endpoint outside
+ * [0, n) gives TEC_EINVAL (nothing is written outside the array), and the next
+ * call starts afresh.
  *
  * Allocates nothing: the union-find parents live in one device array of
  * TEC_NOALLOC_MAX_VERTICES int32 (16 MiB) that every GPU loading the library
  * holds until the process exits.  The first call on a device looks up that
- * array's device address, so make it before any stream capture.  All calls on
+ * array's device address, so make it before any stream capture.  The address
+ * is kept for the life of the process: do not call this entry point on a
+ * device after a cudaDeviceReset of it (the module, and with it the array, is
+ * loaded anew, and the kept address is stale).  All calls on
  * a device share the array and each call re-initialises it; calls whose GPU
  * work overlaps (other streams, other host threads) race on it and must be
  * serialised by the caller. */

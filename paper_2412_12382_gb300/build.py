@@ -41,7 +41,7 @@ def _sources(csrc: str = CSRC):
 
 
 def _deps():
-    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
+    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))) + [
         os.path.join(os.path.dirname(HERE), "include", "tectonic.h")]
 
 

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <atomic>
 
+#include "msf_key.h"
 #include "tec_internal.cuh"
 #include "uf.cuh"
 
@@ -30,9 +31,7 @@ namespace {
 
 constexpr uint8_t FOREST_BIT = 0x80;
 
-__device__ __forceinline__ uint64_t msf_key(uint8_t L, int64_t j) {
-    return ((uint64_t)L << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)j);
-}
+__device__ __forceinline__ uint64_t msf_key(uint8_t L, int64_t j) { return msf_key_pack(L, j); }
 
 // Exclusive prefix of per-thread counts over a TILE_THREADS block; *total gets the block sum.
 __device__ __forceinline__ int block_excl_prefix(int c, int *total) {
@@ -205,7 +204,7 @@ __global__ void k_msf_hook(const int64_t *ooff, const int32_t *ocol, uint8_t *lv
         const unsigned long long key = best[r];
         if (!key) continue;
         best[r] = 0ull;
-        const int64_t j = (int64_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
+        const int64_t j = msf_key_edge(key);
         const int32_t u = (int32_t)row_search(ooff, 0, n - 1, j);
         if (uf_link_merged(parent, u, ocol[j], ctr)) {
             lvl[j] |= FOREST_BIT;

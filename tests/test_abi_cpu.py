@@ -113,3 +113,37 @@ def test_debug_build_compiles_and_answers_from_c(tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
+def test_sweep_offer_key_round_trip(tmp_path):
+    """The sweep's packed offer key keeps every edge index a graph can hold
+    (m < 2^40, beyond 2^32) and orders offers by (level, -edge index)."""
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no C++ compiler")
+    src = tmp_path / "key.cc"
+    src.write_text(r'''
+#include <stdio.h>
+#include "msf_key.h"
+using namespace tec;
+int main() {
+    const int64_t js[] = {0, 1, 12345, (1ll << 32) - 1, 1ll << 32, (1ll << 32) + 1, (1ll << 39) - 1, (1ll << 40) - 1};
+    for (int L = 1; L <= 127; ++L)
+        for (int64_t j : js) {
+            const uint64_t k = msf_key_pack((uint8_t)L, j);
+            if (k == 0 || msf_key_edge(k) != j || msf_key_level(k) != L) { printf("bad %d %lld\n", L, (long long)j); return 1; }
+            if (msf_key_pack((uint8_t)L, j + 1) >= k) { printf("order j %lld\n", (long long)j); return 1; }
+            if (L < 127 && msf_key_pack((uint8_t)(L + 1), (1ll << 40) - 1) <= k) { printf("order L\n"); return 1; }
+        }
+    /* two edges 2^32 apart get distinct keys (a 32-bit field would merge them) */
+    if (msf_key_pack(5, 7) == msf_key_pack(5, 7 + (1ll << 32))) { printf("collision\n"); return 1; }
+    printf("ok\n");
+    return 0;
+}
+''')
+    exe = str(tmp_path / "key")
+    r = subprocess.run([gxx, "-std=c++17", "-Wall", "-Werror", "-I", os.path.join(ROOT, "paper_2412_12382_gb300", "csrc"),
+                        str(src), "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=30)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr

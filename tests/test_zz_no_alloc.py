@@ -65,3 +65,23 @@ def test_noalloc_rejects_oversized_input(tec):
     with pytest.raises(tec.TectonicError) as err:
         components_noalloc(NOALLOC_MAX_VERTICES + 1, e, e, labels=torch.empty(1, dtype=torch.int32, device="cuda"))
     assert err.value.status == 1
+
+
+def test_noalloc_rejects_endpoints_outside_the_vertex_range(tec):
+    """An endpoint equal to n or negative is reported as TEC_EINVAL (the hook
+    checks both ends before it touches the scratch), and the next valid call
+    still returns the right labels."""
+    import torch
+    from paper_2412_12382_gb300.tectonic import components_noalloc
+    n = 6
+    for bad_u, bad_v in (([0, 1], [n, 2]), ([-1, 3], [0, 4])):
+        u = torch.tensor(bad_u, dtype=torch.int32, device="cuda")
+        v = torch.tensor(bad_v, dtype=torch.int32, device="cuda")
+        with pytest.raises(tec.TectonicError) as err:
+            components_noalloc(n, u, v)
+        assert err.value.status == 1
+    u = torch.tensor([0, 1, 4], dtype=torch.int32, device="cuda")
+    v = torch.tensor([2, 2, 5], dtype=torch.int32, device="cuda")
+    lab, nc = components_noalloc(n, u, v)
+    assert nc == 3
+    assert lab.cpu().tolist() == [0, 0, 0, 3, 4, 4]

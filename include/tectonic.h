@@ -54,7 +54,9 @@ typedef enum tec_status {
     TEC_EOVERFLOW = 5,  /* a size or threshold does not fit the checked integer width */
     TEC_EBADGRAPH = 6,  /* validation found an unsorted row, self-loop, duplicate or asymmetry,
                            or a label or block id was out of range */
-    TEC_ESTATE = 7      /* a call needs a step that has not been run (e.g. components before prune) */
+    TEC_ESTATE = 7,     /* a call needs a step that has not been run (e.g. components before prune) */
+    TEC_EIO = 8         /* a checkpoint file could not be opened, read or written, or is not a valid
+                           picker checkpoint (wrong magic, version, shape, size or checksum) */
 } tec_status;
 
 /* Similarity functions of Table 1. */
@@ -343,6 +345,32 @@ tec_status tec_picker_get_params(tec_picker *p, float *params_out, float *adam_m
                                  int64_t *step_out);
 tec_status tec_picker_set_params(tec_picker *p, const float *params, const float *adam_m, const float *adam_v,
                                  int64_t step);
+
+/* Checkpoint files, so that a C client can train, keep and reload a picker
+ * (the parameters, both Adam moments, the step count and a free-form UTF-8
+ * "meta" text such as the training record).  Format, all little-endian:
+ * magic "TECPICK1"; uint32 version 1; uint32 inputs, hidden and parameter
+ * counts (66, 128, 25217); int64 step; uint32 meta length L; L meta bytes;
+ * then parameters, first moments and second moments, TEC_PICKER_PARAMS
+ * IEEE binary32 values each; last a uint64 FNV-1a 64-bit hash of every byte
+ * before it.  A file that does not match it byte for byte is TEC_EIO.
+ *
+ * tec_picker_file_write / _read work on HOST arrays and need no device:
+ * write stores params (required), adam_m / adam_v (NULL = zeros), step and
+ * meta (NUL-terminated, NULL = empty); read checks the whole file and copies
+ * out what is asked for (any output may be NULL): params, moments and step,
+ * up to meta_cap - 1 meta bytes plus a terminator into meta, and the full
+ * meta length into *meta_len.  tec_picker_save writes a picker's current
+ * state (waits for its stream); tec_picker_load creates a picker on the
+ * current device (stream as in tec_picker_create) holding the file's state,
+ * so training resumes where it stopped.  Not from the paper: the picker
+ * replaces the rules of thumb of Sec. IV-D. */
+tec_status tec_picker_file_write(const char *path, const float *params, const float *adam_m, const float *adam_v,
+                                 int64_t step, const char *meta);
+tec_status tec_picker_file_read(const char *path, float *params, float *adam_m, float *adam_v, int64_t *step,
+                                char *meta, size_t meta_cap, size_t *meta_len);
+tec_status tec_picker_save(tec_picker *p, const char *path, const char *meta);
+tec_status tec_picker_load(const char *path, void *stream, tec_picker **out);
 
 /* out[i] = network output for feats row i (device, N x 66 float32 in, N
  * float32 out).  bf16 != 0 rounds inputs, weights and hidden activations to

@@ -98,6 +98,164 @@ void orc_edge_counts(const int64_t *off, const int32_t *col, int64_t m,
     }
 }
 
+/* Per-edge triangle counts t(u,v) = |N(u) n N(v)| (Sec. I) by oriented
+ * triangle listing -- the textbook "forward" algorithm (Chiba & Nishizeki
+ * 1985; Schank & Wagner 2005) -- for graphs on which the per-edge merges of
+ * Sec. III-C cost too much (their work is the sum over edges of
+ * deg u + deg v, quadratic in the hub degrees).
+ *
+ *   1. Rank the vertices by (degree, id) ascending (a stable counting sort by
+ *      degree); rank_of[v] is v's position and order[i] the vertex of rank i.
+ *   2. Orient every edge from its lower-ranked to its higher-ranked end:
+ *      out-row i holds the ranks of the higher-ranked neighbours of order[i].
+ *   3. For every rank a: mark the heads of out-row a; for every head b of
+ *      out-row a and every head c of out-row b, a marked c closes the
+ *      triangle a < b < c, which is found only here (c is not in out-row a
+ *      of any other pair, and b is not in out-row c).  The triangle adds one
+ *      to each of its three oriented edges a->b, a->c, b->c.
+ *   4. Every oriented edge is one undirected edge {U, V}; its count goes to
+ *      the canonical id of (min, max): the upper-triangle entries before row
+ *      min plus the position of max among row min's entries above min,
+ *      found by binary search in the sorted row.
+ * Additions commute, so the counts do not depend on the thread count.
+ * t_out: m uint32 in canonical order.  Returns 0, or -1 if out of memory. */
+int orc_forward_counts(int64_t n, const int64_t *off, const int32_t *col, uint32_t *t_out, int nthreads)
+{
+    if (n <= 0) return 0;
+    if (nthreads < 1) nthreads = 1;
+    const int64_t nnz = off[n], m = nnz / 2;
+    int64_t maxdeg = 0;
+    for (int64_t v = 0; v < n; ++v)
+        if (off[v + 1] - off[v] > maxdeg) maxdeg = off[v + 1] - off[v];
+    int64_t *start = (int64_t *)calloc((size_t)maxdeg + 2, sizeof(int64_t));
+    int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *rank_of = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int64_t *roff = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int64_t *uoff = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int32_t *rcol = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+    uint32_t *rt = (uint32_t *)calloc((size_t)(m > 0 ? m : 1), sizeof(uint32_t));
+    int fail = !start || !order || !rank_of || !roff || !uoff || !rcol || !rt;
+    if (fail) goto done;
+    /* 1. stable counting sort by degree */
+    for (int64_t v = 0; v < n; ++v) start[off[v + 1] - off[v] + 1]++;
+    for (int64_t d = 0; d <= maxdeg; ++d) start[d + 1] += start[d];
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t i = start[off[v + 1] - off[v]]++;
+        order[i] = (int32_t)v;
+        rank_of[v] = (int32_t)i;
+    }
+    /* 2. out-rows in rank space: lengths, their prefix sums, then the heads */
+    roff[0] = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4096) num_threads(nthreads)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t u = order[i];
+        int64_t c = 0;
+        for (int64_t k = off[u]; k < off[u + 1]; ++k) c += rank_of[col[k]] > i;
+        roff[i + 1] = c;
+    }
+    for (int64_t i = 0; i < n; ++i) roff[i + 1] += roff[i];
+    if (roff[n] != m) { fail = 1; goto done; }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4096) num_threads(nthreads)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t u = order[i];
+        int64_t j = roff[i];
+        for (int64_t k = off[u]; k < off[u + 1]; ++k)
+            if (rank_of[col[k]] > i) rcol[j++] = rank_of[col[k]];
+    }
+    /* 3. list every triangle once, from its lowest-ranked vertex */
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        /* mark[c] = 1 + position of c in the current out-row a, 0 = unmarked;
+         * acc[x] = triangles found so far on the edge a -> (x-th head of a).
+         * Other threads add to the same edges (as their b -> c), so every
+         * addition to rt is atomic; the edges of row a are added once per
+         * row from acc. */
+        uint32_t *mark = (uint32_t *)calloc((size_t)n, sizeof(uint32_t));
+        uint64_t *bits = (uint64_t *)calloc((size_t)(n + 63) / 64, sizeof(uint64_t));   /* mark[c] != 0 */
+        uint32_t *acc = (uint32_t *)calloc((size_t)maxdeg + 1, sizeof(uint32_t));
+        if (!mark || !bits || !acc) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            fail = 1;
+        }
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+        for (int64_t a = 0; a < n; ++a) {
+            if (!mark || !bits || !acc) continue;
+            const int64_t ab = roff[a], ae = roff[a + 1];
+            for (int64_t j = ab; j < ae; ++j) {
+                mark[rcol[j]] = (uint32_t)(j - ab + 1);
+                bits[rcol[j] >> 6] |= (uint64_t)1 << (rcol[j] & 63);
+                acc[j - ab] = 0u;
+            }
+            for (int64_t j = ab; j < ae; ++j) {
+                const int32_t b = rcol[j];
+                uint32_t hits = 0;
+                for (int64_t k = roff[b]; k < roff[b + 1]; ++k) {
+                    const int32_t c = rcol[k];
+                    if ((bits[c >> 6] >> (c & 63)) & 1u) {
+                        const uint32_t x = mark[c];
+                        ++hits;                                               /* a -> b */
+                        ++acc[x - 1];                                         /* a -> c */
+                        __atomic_fetch_add(&rt[k], 1u, __ATOMIC_RELAXED);     /* b -> c */
+                    }
+                }
+                acc[j - ab] += hits;
+            }
+            for (int64_t j = ab; j < ae; ++j) {
+                mark[rcol[j]] = 0u;
+                bits[rcol[j] >> 6] = 0u;
+                if (acc[j - ab]) __atomic_fetch_add(&rt[j], acc[j - ab], __ATOMIC_RELAXED);
+            }
+        }
+        free(mark);
+        free(bits);
+        free(acc);
+    }
+    if (fail) goto done;
+    /* 4. canonical ids: uoff[u] = upper-triangle entries in rows before u */
+    uoff[0] = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4096) num_threads(nthreads)
+#endif
+    for (int64_t u = 0; u < n; ++u) {
+        int64_t lo = off[u], hi = off[u + 1];
+        while (lo < hi) {                        /* first entry above u */
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (col[mid] < u) lo = mid + 1; else hi = mid;
+        }
+        uoff[u + 1] = off[u + 1] - lo;
+    }
+    for (int64_t u = 0; u < n; ++u) uoff[u + 1] += uoff[u];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4096) num_threads(nthreads)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = roff[i]; j < roff[i + 1]; ++j) {
+            const int64_t x = order[i], y = order[rcol[j]];
+            const int64_t a = x < y ? x : y, b = x < y ? y : x;
+            int64_t lo = off[a], hi = off[a + 1];
+            while (lo < hi) {                    /* position of b in row a */
+                const int64_t mid = lo + (hi - lo) / 2;
+                if (col[mid] < b) lo = mid + 1; else hi = mid;
+            }
+            const int64_t above = off[a + 1] - (uoff[a + 1] - uoff[a]);   /* first entry above a */
+            t_out[uoff[a] + (lo - above)] = rt[j];
+        }
+    }
+done:
+    free(start); free(order); free(rank_of); free(roff); free(uoff); free(rcol); free(rt);
+    return fail ? -1 : 0;
+}
+
 /* K4 participation (Table 1, kappa = 4): for each edge e = (u, v) the number
  * of 4-cliques containing it, i.e. the number of edges {c, d} with both ends
  * in the common neighbourhood C = N(u) n N(v).  C is built by merging the two

@@ -87,7 +87,7 @@ def substitute(text: str, name: str, value: int) -> str:
 def source_hash() -> str:
     h = hashlib.sha256()
     for path in sorted(os.listdir(_build.CSRC)):
-        if path.endswith((".cu", ".cuh")):
+        if path.endswith((".cu", ".cuh", ".h")):
             h.update(path.encode())
             h.update(open(os.path.join(_build.CSRC, path), "rb").read())
     h.update(open(os.path.join(INCLUDE, "tectonic.h"), "rb").read())
@@ -122,7 +122,7 @@ def write_variant_sources(overrides: dict, root: str) -> str:
             raise ValueError(f"{name} is not a tunable")
         by_file.setdefault(TUNABLES[name][0], []).append((name, value))
     for fname in os.listdir(_build.CSRC):
-        if not fname.endswith((".cu", ".cuh")):
+        if not fname.endswith((".cu", ".cuh", ".h")):
             continue
         text = open(os.path.join(_build.CSRC, fname)).read()
         for name, value in by_file.get(fname, []):

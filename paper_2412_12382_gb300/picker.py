@@ -149,27 +149,24 @@ def evaluate(picker, dataset, bf16=False, baseline_level=None):
     return out
 
 
+CHECKPOINT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "picker_weights.tecp")
+
+
 def save(picker, path, meta=None):
+    """Writes a checkpoint file in the library's format (tec_picker_file_write):
+    parameters, Adam moments, step and the training record as JSON text."""
     params, m, v, step = picker.get_params(with_adam=True)
-    digest = hashlib.sha256(params.tobytes() + m.tobytes() + v.tobytes()).hexdigest()
-    np.savez(path, params=params, adam_m=m, adam_v=v, step=np.int64(step),
-             meta=json.dumps(meta or {}), sha256=digest)
+    T.picker_file_write(path, params, m, v, step, json.dumps(meta or {}))
 
 
 def read_checkpoint(path):
-    """The arrays of a checkpoint written by `save`, after checking the sha256
-    of parameters and Adam moments (host only; ValueError on a mismatch)."""
-    d = np.load(path, allow_pickle=False)
-    params, m, v = d["params"], d["adam_m"], d["adam_v"]
-    if params.shape != (T.PICKER_PARAMS,) or m.shape != params.shape or v.shape != params.shape:
-        raise ValueError(f"checkpoint {path} does not hold {T.PICKER_PARAMS} parameters and moments")
-    if hashlib.sha256(params.tobytes() + m.tobytes() + v.tobytes()).hexdigest() != str(d["sha256"]):
-        raise ValueError(f"checkpoint {path} fails its checksum")
-    return params, m, v, int(d["step"]), json.loads(str(d["meta"]))
+    """The arrays of a checkpoint file, checked by the library (host only;
+    TectonicError TEC_EIO when the file is damaged or not a checkpoint)."""
+    params, m, v, step, meta = T.picker_file_read(path)
+    return params, m, v, step, json.loads(meta or "{}")
 
 
 def load(path):
-    params, m, v, step, meta = read_checkpoint(path)
-    picker = T.Picker(params)
-    picker.set_params(params, m, v, step)
-    return picker, meta
+    """A device picker holding the file's state (tec_picker_load) and its record."""
+    meta = read_checkpoint(path)[4]
+    return T.Picker.load(path), meta

@@ -69,6 +69,11 @@ SIGNATURES = {
     "tec_picker_free": ([_P], ctypes.c_int),
     "tec_picker_get_params": ([_P, _P, _P, _P, _PI64], ctypes.c_int),
     "tec_picker_set_params": ([_P, _P, _P, _P, _I64], ctypes.c_int),
+    "tec_picker_file_write": ([ctypes.c_char_p, _P, _P, _P, _I64, ctypes.c_char_p], ctypes.c_int),
+    "tec_picker_file_read": ([ctypes.c_char_p, _P, _P, _P, _PI64, ctypes.c_char_p, ctypes.c_size_t,
+                              ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "tec_picker_save": ([_P, ctypes.c_char_p, ctypes.c_char_p], ctypes.c_int),
+    "tec_picker_load": ([ctypes.c_char_p, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "tec_picker_forward": ([_P, _P, _I64, ctypes.c_int, _P], ctypes.c_int),
     "tec_picker_loss_grad": ([_P, _P, _P, _I64, _P, _P], ctypes.c_int),
     "tec_picker_adam_step": ([_P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float], ctypes.c_int),
@@ -460,16 +465,56 @@ def picker_thresholds(y, stream=None):
     return p, q
 
 
+def picker_file_write(path: str, params, adam_m=None, adam_v=None, step: int = 0, meta: str = ""):
+    """Writes a picker checkpoint file from host arrays (tec_picker_file_write; no device needed)."""
+    arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in (params, adam_m, adam_v)]
+    for a in arrs:
+        if a is not None and a.shape != (PICKER_PARAMS,):
+            raise ValueError(f"a checkpoint holds {PICKER_PARAMS} parameters and moments")
+    check(load_library().tec_picker_file_write(os.fsencode(path), *[_ptr(a) for a in arrs], int(step),
+                                               meta.encode()))
+
+
+def picker_file_read(path: str):
+    """(params, adam_m, adam_v, step, meta text) of a checkpoint file, checked
+    by the library (tec_picker_file_read; no device needed)."""
+    lib = load_library()
+    L = ctypes.c_size_t(0)
+    check(lib.tec_picker_file_read(os.fsencode(path), None, None, None, None, None, 0, ctypes.byref(L)))
+    p, m, v = (np.empty(PICKER_PARAMS, dtype=np.float32) for _ in range(3))
+    step = ctypes.c_int64(0)
+    buf = ctypes.create_string_buffer(L.value + 1)
+    check(lib.tec_picker_file_read(os.fsencode(path), _ptr(p), _ptr(m), _ptr(v), ctypes.byref(step), buf,
+                                   L.value + 1, ctypes.byref(L)))
+    return p, m, v, step.value, buf.raw[:L.value].decode()
+
+
 class Picker:
     """The learned threshold picker (a ``tec_picker``)."""
 
-    def __init__(self, init_params=None, stream=None):
+    def __init__(self, init_params=None, stream=None, _handle=None):
         torch = _require_cuda()
         self._lib = load_library()
         self.stream = stream or torch.cuda.current_stream()
         self._h = _P()
+        if _handle is not None:
+            self._h = _handle
+            return
         init = None if init_params is None else np.ascontiguousarray(init_params, dtype=np.float32)
         check(self._lib.tec_picker_create(_ptr(init), _P(self.stream.cuda_stream), ctypes.byref(self._h)))
+
+    @classmethod
+    def load(cls, path: str, stream=None):
+        """A picker holding the state of a checkpoint file (tec_picker_load)."""
+        torch = _require_cuda()
+        stream = stream or torch.cuda.current_stream()
+        h = _P()
+        check(load_library().tec_picker_load(os.fsencode(path), _P(stream.cuda_stream), ctypes.byref(h)))
+        return cls(stream=stream, _handle=h)
+
+    def save(self, path: str, meta: str = ""):
+        """Writes the current parameters, Adam moments and step (tec_picker_save)."""
+        check(self._lib.tec_picker_save(self._h, os.fsencode(path), meta.encode()))
 
     def free(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -21,7 +21,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-DEFAULT_OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "picker_weights.npz")
+DEFAULT_OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "picker_weights.tecp")
 
 
 def main(argv=None):

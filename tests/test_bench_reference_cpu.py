@@ -33,6 +33,9 @@ def test_reference_arm_line_on_the_sbm_workload():
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["m"] == 28039 and d["config"]["n"] == 2000
+    # the step time is the one measured (a bounded sample), the full-graph projection a key of its own
+    assert 0 < d["ms_per_step"] < 60_000 and d["ms_per_step_kind"].startswith("measured")
+    assert d["projected_ms_per_full_graph"] > 0 and cb["cpu_model"]
 
 
 def test_reference_arm_without_the_device_generator_is_unavailable():

@@ -3,7 +3,6 @@ weights pass their checksum and carry the training record; a file whose
 parameters, moments or size were changed after saving is refused before
 anything reaches a device; a cached dataset round-trips, is keyed by its
 seeds and size range, and fails loudly when altered."""
-import json
 import os
 
 import numpy as np
@@ -12,39 +11,49 @@ import pytest
 from paper_2412_12382_gb300 import picker as P
 from paper_2412_12382_gb300 import tectonic as T
 
-SHIPPED = os.path.join(os.path.dirname(P.__file__), "picker_weights.npz")
+SHIPPED = os.path.join(os.path.dirname(P.__file__), "picker_weights.tecp")
+HEADER = 36
 
 
 def test_shipped_weights_verify():
     params, m, v, step, meta = P.read_checkpoint(SHIPPED)
     assert params.dtype == np.float32 and params.shape == (T.PICKER_PARAMS,)
     assert np.isfinite(params).all() and step > 0
-    assert isinstance(meta, dict)
+    assert isinstance(meta, dict) and "eval" in meta
 
 
-def _rewrite(src, dst, **changes):
-    d = dict(np.load(src, allow_pickle=False))
-    d.update(changes)
-    np.savez(dst, **d)
+def _meta_len(raw):
+    return int.from_bytes(raw[32:36], "little")
 
 
-@pytest.mark.parametrize("field", ["params", "adam_m", "adam_v"])
+def _refused(path, what):
+    with pytest.raises(T.TectonicError) as e:
+        P.read_checkpoint(path)
+    assert e.value.status == 8 and what in str(e.value)
+
+
+@pytest.mark.parametrize("field", [0, 1, 2])
 def test_tampered_arrays_are_refused(tmp_path, field):
-    d = np.load(SHIPPED, allow_pickle=False)
-    bad = d[field].copy()
-    bad[12345] = np.nextafter(bad[12345], np.float32(np.inf))    # one ulp in one entry
-    path = str(tmp_path / "bad.npz")
-    _rewrite(SHIPPED, path, **{field: bad})
-    with pytest.raises(ValueError, match="checksum"):
-        P.read_checkpoint(path)
+    # one bit of one entry of the parameters, the first or the second moments
+    raw = bytearray(open(SHIPPED, "rb").read())
+    at = HEADER + _meta_len(raw) + 4 * (field * T.PICKER_PARAMS + 12345)
+    raw[at] ^= 1
+    path = str(tmp_path / "bad.tecp")
+    open(path, "wb").write(raw)
+    _refused(path, "checksum")
 
 
-def test_wrong_size_is_refused(tmp_path):
-    d = np.load(SHIPPED, allow_pickle=False)
-    path = str(tmp_path / "short.npz")
-    _rewrite(SHIPPED, path, params=d["params"][:-1])
-    with pytest.raises(ValueError, match="parameters"):
-        P.read_checkpoint(path)
+def test_wrong_size_shape_and_magic_are_refused(tmp_path):
+    raw = open(SHIPPED, "rb").read()
+    cases = {"short": raw[:-4], "magic": b"XECPICK1" + raw[8:],
+             "shape": raw[:20] + (T.PICKER_PARAMS - 1).to_bytes(4, "little") + raw[24:],
+             "version": raw[:8] + (2).to_bytes(4, "little") + raw[12:]}
+    expect = {"short": "size", "magic": "not a picker checkpoint", "shape": "shape", "version": "version"}
+    for name, data in cases.items():
+        path = str(tmp_path / f"{name}.tecp")
+        open(path, "wb").write(data)
+        _refused(path, expect[name])
+    _refused(str(tmp_path / "missing.tecp"), "cannot open")
 
 
 def test_round_trip_of_a_new_checkpoint(tmp_path):
@@ -57,12 +66,31 @@ def test_round_trip_of_a_new_checkpoint(tmp_path):
         def get_params(self, with_adam=False):
             return params, m, v, 17
 
-    path = str(tmp_path / "new.npz")
+    path = str(tmp_path / "new.tecp")
     P.save(FakePicker(), path, {"epochs": 3})
     p2, m2, v2, step, meta = P.read_checkpoint(path)
     assert np.array_equal(p2, params) and np.array_equal(m2, m) and np.array_equal(v2, v)
     assert step == 17 and meta == {"epochs": 3}
-    assert json.loads(str(np.load(path)["meta"])) == {"epochs": 3}
+
+
+def test_file_layout_is_the_documented_one(tmp_path):
+    """The bytes follow the layout of the header: magic, version, shape,
+    step, meta, three little-endian float32 arrays, FNV-1a 64 of the rest
+    (computed here from its published definition)."""
+    params = np.arange(T.PICKER_PARAMS, dtype=np.float32) / 7
+    path = str(tmp_path / "layout.tecp")
+    T.picker_file_write(path, params, None, None, -5, "ab")
+    raw = open(path, "rb").read()
+    assert raw[:8] == b"TECPICK1"
+    assert [int.from_bytes(raw[i:i + 4], "little") for i in (8, 12, 16, 20)] == [1, 66, 128, T.PICKER_PARAMS]
+    assert int.from_bytes(raw[24:32], "little", signed=True) == -5
+    assert _meta_len(raw) == 2 and raw[36:38] == b"ab"
+    body = np.frombuffer(raw[38:38 + 12 * T.PICKER_PARAMS], dtype="<f4")
+    assert np.array_equal(body[:T.PICKER_PARAMS], params) and not body[T.PICKER_PARAMS:].any()
+    h = 0xCBF29CE484222325
+    for b in raw[:-8]:
+        h = ((h ^ b) * 0x100000001B3) & 0xFFFFFFFFFFFFFFFF
+    assert int.from_bytes(raw[-8:], "little") == h and len(raw) == 38 + 12 * T.PICKER_PARAMS + 8
 
 
 def _fake_dataset(torch, seed=0, graphs=7):

@@ -77,11 +77,18 @@ def test_training_fits_and_checkpoint_round_trip(tec, tmp_path):
     pk = Picker(P.init_params(1))
     losses = pk.train(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda(), epochs=60, batch=128, lr=2e-3, seed=7)
     assert losses[-1] < 0.05 * losses[0]
-    path = str(tmp_path / "pk.npz")
+    path = str(tmp_path / "pk.tecp")
     P.save(pk, path, {"note": "test"})
     pk2, meta = P.load(path)
     Xd = torch.from_numpy(X[:50]).cuda()
     assert torch.equal(pk.forward(Xd), pk2.forward(Xd)) and meta["note"] == "test"
+    # the library's own save of the loaded picker reproduces the file byte for byte
+    pk2.save(str(tmp_path / "again.tecp"), open(path, "rb").read()[36:36 + len('{"note": "test"}')].decode())
+    assert open(path, "rb").read() == open(str(tmp_path / "again.tecp"), "rb").read()
+    # training resumes from the loaded Adam state exactly as from the original
+    pk.train(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda(), epochs=2, batch=128, lr=2e-3, seed=9)
+    pk2.train(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda(), epochs=2, batch=128, lr=2e-3, seed=9)
+    assert np.array_equal(pk.get_params(), pk2.get_params())
     pk.free()
     pk2.free()
 
@@ -146,4 +153,51 @@ def test_pick_threshold_equals_features_forward_thresholds(tec):
     pr1, qr1 = T.picker_thresholds(pk.forward(g1.features()))
     assert p1.shape == (1,) and torch.equal(p1, pr1) and torch.equal(q1, qr1)
     g1.free()
+    pk.free()
+
+
+def test_c_client_loads_the_shipped_picker_and_picks(tec, tmp_path):
+    """A C program linked only against the library (and the CUDA runtime for
+    its two output buffers) loads the shipped checkpoint, picks the threshold
+    of a graph in float32 and bfloat16, prunes and labels at it, and writes
+    the picker back byte for byte; its thresholds equal the Python binding's."""
+    import os
+    import shutil
+    import subprocess
+    import torch
+    from graphgen.dcsbm import dcsbm_csr
+    from paper_2412_12382_gb300 import build as libbuild
+    from paper_2412_12382_gb300 import picker as P
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    libdir = os.path.dirname(libbuild.library_path())
+    exe = str(tmp_path / "picker_client")
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(root, "include"),
+                        "-I", os.path.join(cuda, "include"), os.path.join(root, "tests", "abi_c", "picker_client.c"),
+                        "-o", exe, "-L", libdir, "-ltectonic", "-L", os.path.join(cuda, "lib64"), "-lcudart",
+                        f"-Wl,-rpath,{libdir}", f"-Wl,-rpath,{os.path.join(cuda, 'lib64')}"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    off, col = dcsbm_csr(20007, 1000, 100000)[:2]
+    gpath = str(tmp_path / "graph.bin")
+    with open(gpath, "wb") as f:
+        f.write(np.array([len(off) - 1, len(col)], dtype=np.int64).tobytes())
+        f.write(np.asarray(off, dtype=np.int64).tobytes())
+        f.write(np.asarray(col, dtype=np.int32).tobytes())
+    out = str(tmp_path / "copy.tecp")
+    r = subprocess.run([exe, P.CHECKPOINT, gpath, out], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    p32, q32, p16, q16, kept, ncomp = (int(x) for x in r.stdout.split())
+    assert open(out, "rb").read() == open(P.CHECKPOINT, "rb").read()
+    pk, _ = P.load(P.CHECKPOINT)
+    g = tec.Graph(torch.from_numpy(np.asarray(off, dtype=np.int64)).cuda(), torch.from_numpy(np.asarray(col)).cuda())
+    for bf16, (pc, qc) in ((False, (p32, q32)), (True, (p16, q16))):
+        p, q = g.pick_threshold(pk, bf16=bf16)
+        assert (int(p[0]), int(q[0])) == (pc, qc)
+    ref = O.full_pass(off, col, O.TECTONIC, p32, q32)
+    assert ncomp == ref.ncomp and kept == int(ref.keep.sum())
+    g.free()
     pk.free()

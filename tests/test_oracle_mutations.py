@@ -47,6 +47,13 @@ C_MUTANTS = [
      "components labelled by their largest vertex id"),
     ("int64_t x = off[c], xend = off[c + 1], y = a + 1;", "int64_t x = off[c], xend = off[c + 1], y = 0;",
      "K4 counts every inner edge of C twice"),
+    ("++hits;                                               /* a -> b */", "/* a -> b dropped */",
+     "forward listing never credits the edge a -> b"),
+    ("__atomic_fetch_add(&rt[k], 1u, __ATOMIC_RELAXED);     /* b -> c */",
+     "__atomic_fetch_add(&rt[j], 1u, __ATOMIC_RELAXED);     /* b -> c */",
+     "forward listing credits b -> c to a -> b"),
+    ("acc[j - ab] += hits;", "acc[j - ab] = hits;",
+     "forward listing overwrites the a -> c credits of an edge with its a -> b hits"),
 ]
 
 PY_MUTANTS = [

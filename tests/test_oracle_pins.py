@@ -517,3 +517,64 @@ def test_k4_participation_closed_forms_and_brute_force():
         assert int(k4.sum()) == 6 * len(cliques)
         keep, kept = O.prune(O.K4, off, eu, ev, None, None, 3, 2, k4)
         assert list(keep) == [1 if 2 * int(x) >= 3 else 0 for x in k4]
+
+
+# ----------------------------------------------------------- forward (oriented) counts
+
+
+def test_forward_counts_brute_force_and_dense_identities():
+    # the oriented listing against set intersections, (A^2)_uv and trace(A^3) = 6T
+    for off, col in _rand_graphs(12, seed=21):
+        nb = _nbrs(off, col)
+        eu, ev = O.edge_list(off, col)
+        t = O.forward_counts(off, col, nthreads=2)
+        for e, (u, v) in enumerate(zip(eu, ev)):
+            assert t[e] == len(nb[u] & nb[v])
+        A = dense_adjacency(off, col)
+        A2 = A @ A
+        assert (t.astype(np.int64) == A2[eu, ev]).all()
+        assert 2 * int(t.sum()) == int(np.trace(A2 @ A))
+        # with the merge's union: deg u + deg v - t (inclusion-exclusion)
+        _, uni = O.edge_counts(off, col, eu, ev)
+        assert np.array_equal(O.unions_from_counts(off, eu, ev, t), uni)
+
+
+@pytest.mark.parametrize("graph,expect", [
+    (small.complete(12), 10), (small.star(25), 0), (small.cycle(7), 0), (small.empty(6), None),
+    (small.empty(1), None),
+])
+def test_forward_counts_closed_forms(graph, expect):
+    off, col = graph
+    t = O.forward_counts(off, col)
+    if expect is None:
+        assert t.size == 0
+    else:
+        assert (t == expect).all()
+
+
+def test_forward_counts_two_cliques_bridge():
+    # interior edges of K_a carry a - 2 triangles, the bridge none
+    a, b = 7, 5
+    off, col = small.two_cliques_bridge(a, b)
+    eu, ev = O.edge_list(off, col)
+    t = O.forward_counts(off, col)
+    inside_a = (eu < a) & (ev < a)
+    inside_b = (eu >= a) & (ev >= a)
+    assert (t[inside_a] == a - 2).all() and (t[inside_b] == b - 2).all()
+    assert (t[~inside_a & ~inside_b] == 0).all()
+
+
+@pytest.mark.parametrize("which", ["gnp", "sbm", "rmat13", "rmat16", "rmat18"])
+def test_forward_counts_equal_the_merges(which):
+    # bit for bit against the per-edge merges of Sec. III-C, on graphs with
+    # hubs, many degree ties and isolated vertices, and for any thread count
+    from graphgen import planted_partition, rmat_csr
+    if which == "gnp":
+        off, col = small.gnp(1500, 0.03, np.random.default_rng(4))
+    elif which == "sbm":
+        off, col, _ = planted_partition(4, 500, 0.05, 0.002, seed=1)
+    else:
+        off, col = rmat_csr(int(which[4:]), 16, seed=2)
+    t, _ = O.edge_counts(off, col, nthreads=O.threads_available())
+    for th in (1, O.threads_available()):
+        assert np.array_equal(O.forward_counts(off, col, nthreads=th), t)

@@ -170,7 +170,9 @@ tec_status tec_prune(tec_graph *g, tec_measure measure, int64_t p, int64_t q, ui
  * prune has run. */
 tec_status tec_components(tec_graph *g, int32_t *labels_out, int64_t *ncomp_out);
 
-/* Components at k thresholds at once: for each threshold i, the labels (and
+/* Algorithm 1 repeated for k thresholds delta_i = p[i]/q[i], as the paper
+ * does when it sweeps delta (Sec. IV-D, Fig. 6; Table 4's TW grid), in one
+ * call.  Components at k thresholds at once: for each threshold i, the labels (and
  * number of components) that tec_prune(p[i], q[i]) + tec_components would give,
  * through a maximum spanning forest of the edge levels (the number of
  * thresholds each edge survives) and one offline union-find sweep over the
@@ -180,7 +182,10 @@ tec_status tec_components(tec_graph *g, int32_t *labels_out, int64_t *ncomp_out)
  * disjoint union: seg_off (device, nseg+1 int64 vertex offsets of the graphs,
  * or NULL) makes every label relative to its graph's first vertex, and
  * ncomp_out (HOST, may be NULL; waits) receives k x nseg component counts (k
- * counts without segments).  Replaces the last prune's mask state.  Without
+ * counts without segments).  This segment table is the batch interface: a
+ * batch of many graphs (for example the 256 degree-corrected SBM graphs of
+ * one sweep launch) is tec_graph_load of their disjoint union plus seg_off,
+ * so no separate batch upload or batch sweep call is needed.  Replaces the last prune's mask state.  Without
  * ncomp_out the call does not wait: device-side errors (a forest still
  * growing after ceil(log2 n) + 2 Boruvka rounds, TEC_ETIMEOUT; a malformed
  * forest, TEC_EBADGRAPH) are reported by the next call that waits.  Once a
@@ -299,6 +304,20 @@ tec_status tec_full_pass_host(tec_graph *g, const int64_t *row_off_host, const i
  * triangle counts recomputes them. */
 tec_status tec_set_core_staging(tec_graph *g, int enable);
 
+/* Probe-row tiling of the triangle counts (off by default).  Each oriented
+ * edge is intersected once, from one centre, which probes the candidate's
+ * out-row.  With tiling, the vertex ids are split into `groups` ranges of
+ * about equal out-row volume, and every core centre (see above) with at least
+ * 8 x groups candidates is visited once per range holding some of its
+ * candidates, all visits of the first range first, so that the centres
+ * visited together probe the rows of one range.  Measured on R-MAT scale 26
+ * it is slower at every setting tried (per-visit start-up outweighs the L2
+ * reuse), so the default (0) leaves it off.  groups: -1 or 0 off, 1..4095
+ * that many ranges.  Needs the core staging; without the memory for its lists
+ * it is skipped.  The counts are identical with any setting; the next call
+ * that needs them recomputes them.  TEC_EINVAL for other values. */
+tec_status tec_set_support_tiling(tec_graph *g, int groups);
+
 /* Instrumentation: number of kernels this library has launched in this
  * process so far (all graphs, all devices). */
 long long tec_launch_count(void);
@@ -373,8 +392,12 @@ tec_status tec_picker_save(tec_picker *p, const char *path, const char *meta);
 tec_status tec_picker_load(const char *path, void *stream, tec_picker **out);
 
 /* out[i] = network output for feats row i (device, N x 66 float32 in, N
- * float32 out).  bf16 != 0 rounds inputs, weights and hidden activations to
- * bfloat16 before every product (float32 accumulation). */
+ * float32 out).  bf16 != 0 computes every product on bfloat16 operands
+ * with float32 accumulation: weights and hidden activations are rounded to
+ * bfloat16, and each input is split into two bfloat16 terms (hi = bf16(x),
+ * lo = bf16(x - hi)), since rounding the inputs (the log edge count, about 9
+ * to 14, loses up to 0.03) would change the picked grid level far more often
+ * than rounding the weights. */
 tec_status tec_picker_forward(tec_picker *p, const float *feats, int64_t N, int bf16, float *out);
 
 /* Mean squared error of the N samples (device feats N x 66, target N) into

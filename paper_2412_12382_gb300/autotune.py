@@ -15,8 +15,9 @@ against each variant before it is timed.
 The search is coordinate descent from the current values: each parameter in
 turn takes its best candidate with the others fixed, until a full round
 changes nothing.  Every timed point goes into a JSON cache.  The cache key
-covers the device, the hash of the sources, the command and the metric, so a
-later run resumes and a source change starts afresh.
+covers the device, the workload's size class, the hash of the sources, the
+command and the metric, so a later run resumes, each size class keeps its own
+optimum, and a source change starts afresh.
 
     python -m paper_2412_12382_gb300.autotune --params C_BATCH,B_BATCH \\
         --metric config.stage_ms.support \\
@@ -55,6 +56,9 @@ TUNABLES = {
     "K4_GRAB": ("k4.cu", [1, 2, 4, 8]),
     "VCHUNK_V": ("tec_internal.cuh", [4, 8, 16]),      # vertices per lane in the sweep's vertex passes
     "BS_CHUNK": ("eval.cu", [2048, 4096, 8192, 16384]),
+    "T_BATCH": ("support.cu", [1, 2, 4, 8, 16]),          # candidates per batch of a tiled visit
+    "HEAVY_CAND": ("support.cu", [4, 8, 16, 32, 64]),     # candidates per range for a centre to be tiled
+    "CORE_ORDER": ("support.cu", [0, 1, 2]),                  # core visits: id order, d+ down, d+ up
 }
 
 
@@ -205,13 +209,13 @@ def check_variant(lib: str, check_cmd: str, cwd: str) -> bool:
 
 
 def tune(params, cmd, metric, reps=3, lower_is_better=True, cache_path=None, device="", cwd=None, log=print,
-         check_cmd=None):
+         check_cmd=None, size_class=""):
     cwd = cwd or os.path.dirname(HERE)
     texts = {f: open(os.path.join(_build.CSRC, f)).read() for f in {TUNABLES[p][0] for p in params}}
     start = {p: int_value(current_value(texts[TUNABLES[p][0]], p)) for p in params}
     space = {p: sorted(set(TUNABLES[p][1]) | {start[p]}) for p in params}
-    key = json.dumps({"device": device, "sources": source_hash(), "cmd": cmd, "metric": metric,
-                      "reps": reps, "check": check_cmd})
+    key = json.dumps({"device": device, "size_class": size_class, "sources": source_hash(), "cmd": cmd,
+                      "metric": metric, "reps": reps, "check": check_cmd})
     cache = {}
     if cache_path and os.path.exists(cache_path):
         cache = json.load(open(cache_path))
@@ -261,6 +265,9 @@ def main(argv=None):
                          "'python -m pytest tests/test_gpu_parity.py -m gpu -x -q'")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--cache", default="autotune_cache.json")
+    ap.add_argument("--size-class", default="",
+                    help="label of the workload's size class (e.g. rmat26, rmat22, dcsbm256): the best "
+                         "constants differ between classes, so each has its own cache entries")
     args = ap.parse_args(argv)
     params = [p.strip() for p in args.params.split(",") if p.strip()]
     device = ""
@@ -271,8 +278,9 @@ def main(argv=None):
     except ImportError:
         pass
     start, best, cost, _ = tune(params, args.cmd, args.metric, args.reps, not args.higher_is_better,
-                                args.cache, device, check_cmd=args.check_cmd)
-    print(json.dumps({"start": start, "best": best, "cost": cost, "metric": args.metric}))
+                                args.cache, device, check_cmd=args.check_cmd, size_class=args.size_class)
+    print(json.dumps({"start": start, "best": best, "cost": cost, "metric": args.metric,
+                      "size_class": args.size_class}))
     return 0
 
 

@@ -92,6 +92,25 @@ tec_status check_canaries() {
     return TEC_OK;
 }
 
+// Lowered iteration caps: TEC_DEBUG_LINK_CAP=<k> allows every union-find
+// link k retries (0: a link between two different roots gives up at once),
+// TEC_DEBUG_MSF_ROUNDS=<r> at most r Boruvka rounds in a sweep.  Both are read
+// again by every call that runs the union-find, so a test can lower a cap,
+// see TEC_ETIMEOUT, restore it and call again on the same graph.
+tec_status debug_refresh_caps(tec_graph *g) {
+    const char *s = getenv("TEC_DEBUG_LINK_CAP");
+    const unsigned long long v = (s && *s) ? std::strtoull(s, nullptr, 10) + 1ull : 0ull;
+    TEC_CUDA(cudaMemcpy(&g->ctr[C_DEBUG_LINK_CAP], &v, sizeof(v), cudaMemcpyHostToDevice));
+    return TEC_OK;
+}
+
+int debug_msf_rounds(int rounds) {
+    const char *s = getenv("TEC_DEBUG_MSF_ROUNDS");
+    if (!s || !*s) return rounds;
+    const long r = std::strtol(s, nullptr, 10);
+    return r >= 1 && r < rounds ? (int)r : rounds;
+}
+
 // Failure injection: with TEC_DEBUG_FAIL_ALLOC set, every allocation whose
 // name contains that text fails as if the device were out of memory, so the
 // fallback and retry paths can be driven on purpose.
@@ -99,6 +118,9 @@ bool injected_alloc_failure(const char *what) {
     const char *pat = getenv("TEC_DEBUG_FAIL_ALLOC");
     return pat && *pat && strstr(what, pat) != nullptr;
 }
+#else
+inline tec_status debug_refresh_caps(tec_graph *) { return TEC_OK; }
+inline int debug_msf_rounds(int rounds) { return rounds; }
 #endif
 
 template <typename T>
@@ -146,8 +168,41 @@ void dfree(void *p) {
     cudaFree(p);
 }
 
+void free_tiling(tec_graph *g) {
+    SupportTiling &t = g->tile;
+    void *ptrs[] = {t.gb, t.heavy, t.bu, t.bv, t.items, t.icnt, t.ioff, t.bsum};
+    for (void *p : ptrs) dfree(p);
+    t = SupportTiling();
+}
+
+// Buffers of the probe-row tiling for `groups` ranges; false (tiling off for
+// this count, no error) when they cannot be allocated.
+bool ensure_tiling(tec_graph *g, int groups) {
+    if (g->tile.groups == groups && g->tile.items) return true;
+    if (g->tile_failed_groups == groups) return false;
+    free_tiling(g);
+    SupportTiling t;
+    t.groups = groups;
+    t.heavy_cap = support_heavy_capacity(g->n_cap);
+    t.item_cap = support_item_capacity(g->nnz_cap, groups, t.heavy_cap);
+    const int64_t bsz = (int64_t)(groups + 1) * t.heavy_cap;
+    if (dalloc(&t.gb, groups + 1, "tiling ranges") != TEC_OK || dalloc(&t.heavy, t.heavy_cap, "tiling centres") != TEC_OK ||
+        dalloc(&t.bu, bsz, "tiling row bounds") != TEC_OK || dalloc(&t.bv, bsz, "tiling row bounds") != TEC_OK ||
+        dalloc(&t.items, t.item_cap, "tiling items") != TEC_OK || dalloc(&t.icnt, groups + 1, "tiling counts") != TEC_OK ||
+        dalloc(&t.ioff, groups + 1, "tiling counts") != TEC_OK ||
+        dalloc(&t.bsum, scan_bsum_size(groups), "tiling counts") != TEC_OK) {
+        g->tile = t;
+        free_tiling(g);
+        g->tile_failed_groups = groups;
+        clear_error();
+        return false;
+    }
+    g->tile = t;
+    return true;
+}
+
 void free_graph_memory(tec_graph *g) {
-    void *ptrs[] = {g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->parent, g->tasks,
+    void *ptrs[] = {g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->parent, g->tasks, g->sym_rows, g->or_rows,
                     g->flags, g->tile_cnt, g->tile_base, g->bsum, g->uoff, g->ucnt, g->labels, g->lvl, g->best,
                     g->fu, g->fv, g->bucket, g->thr, g->sw_ncomp, g->seg_hist, g->ari_sums,
                     g->ari_size, g->ari_keys, g->ari_cnt, g->msf_u, g->msf_v, g->msf_k, g->msf_cnt, g->msf_changed,
@@ -155,6 +210,10 @@ void free_graph_memory(tec_graph *g) {
                     g->prf_best, g->prf_bestb, g->prf_sums,
                     g->st_hist, g->st_sums, g->st_cnt_n, g->st_cnt_v, g->ctr};
     for (void *p : ptrs) dfree(p);
+    free_tiling(g);
+    void *order[] = {g->corder.hist, g->corder.base, g->corder.bsum, g->corder.sorted};
+    for (void *p : order) dfree(p);
+    g->corder = CoreOrder();
     if (g->ctr_host) cudaFreeHost(g->ctr_host);
 }
 
@@ -185,8 +244,9 @@ tec_status reset_counter(tec_graph *g, int which) {
 
 tec_status ensure_oriented(tec_graph *g) {
     if (g->oriented) return TEC_OK;
-    TEC_CUDA(launch_orient(g->off, g->col, g->deg, g->n, g->nnz, g->flags, g->tile_cnt, g->tile_base,
+    TEC_CUDA(launch_orient(g->off, g->col, g->deg, g->n, g->nnz, g->sym_rows, g->flags, g->tile_cnt, g->tile_base,
                            g->bsum, g->ooff, g->ocol, g->m, g->ctr, g->stream));
+    TEC_CUDA(launch_tile_rows(g->ooff, g->n, g->m, g->or_rows, g->stream));
     g->oriented = true;
     g->supported = g->pruned = g->hooked = false;
     return TEC_OK;
@@ -215,6 +275,19 @@ tec_status ensure_support(tec_graph *g) {
             clear_error();
         } else {
             g->core_state = 1;
+            // optional: the visit order by out-degree (without it, the visits run as emitted)
+            const int64_t oc = core_order_classes();
+            CoreOrder o;
+            if (oc > 0 && (dalloc(&o.hist, oc + 1, "core visit order") != TEC_OK ||
+                           dalloc(&o.base, oc + 1, "core visit order") != TEC_OK ||
+                           dalloc(&o.bsum, scan_bsum_size(oc), "core visit order") != TEC_OK ||
+                           dalloc(&o.sorted, g->task_cap, "core visit order") != TEC_OK)) {
+                void *part[] = {o.hist, o.base, o.bsum, o.sorted};
+                for (void *q2 : part) dfree(q2);
+                o = CoreOrder();
+                clear_error();
+            }
+            g->corder = o;
         }
     }
     const bool core = g->core_state > 0 && g->core_enabled;
@@ -224,9 +297,14 @@ tec_status ensure_support(tec_graph *g) {
                                     reinterpret_cast<long long *>(g->core_hist + 33), g->core_tc,
                                     g->core_tc + tiles + 32, g->bsum, g->core_of, g->pv2, g->stream));
     }
+    // probe-row tiling (needs the core staging): automatic range count unless set
+    int groups = g->tile_request < 0 ? 0 : g->tile_request > 0 ? g->tile_request : support_auto_groups(g->m);
+    if (!core || (groups > 0 && !ensure_tiling(g, groups))) groups = 0;
+    SupportTiling tl = g->tile;
+    if (!groups) tl.groups = 0;
     TEC_CUDA(launch_support(g->off, g->col, g->flags, g->ooff, g->ocol, g->n, g->m, g->t, g->tasks, g->task_cap,
                             g->ctr, g->num_sms, g->stream, core ? g->pv2 : nullptr, core ? g->core_of : nullptr,
-                            core ? g->ctasks : nullptr));
+                            core ? g->ctasks : nullptr, tl, g->corder));
     ++g->support_epoch;
     g->supported = true;
     g->pruned = g->hooked = false;
@@ -300,7 +378,7 @@ tec_status run_full_pass(tec_graph *g, int measure, int64_t p, int64_t q, int32_
     TEC_TRY(reset_counter(g, C_NCOMP));
     TEC_CUDA(launch_cc_init(g->parent, g->n, g->stream));
     PruneArgs a{cmp, p, q, true};
-    TEC_CUDA(launch_prune(g->ooff, g->ocol, g->deg, cts, g->n, g->m, a, g->keep, g->parent, g->ctr, g->stream));
+    TEC_CUDA(launch_prune(g->ooff, g->ocol, g->deg, cts, g->n, g->m, g->or_rows, a, g->keep, g->parent, g->ctr, g->stream));
     g->pruned = g->hooked = true;
     g->last_measure = measure;
     g->last_p = p;
@@ -381,7 +459,7 @@ tec_status tec_features(tec_graph *g, const int64_t *seg_off, int nseg, float *f
     const int ns = seg_off ? nseg : 1;
     TEC_TRY(ensure_seg_scratch(g, ns));
     TEC_TRY(ensure_support(g));
-    TEC_CUDA(launch_features(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, seg_off, nseg, g->seg_hist, feat_out, g->ctr,
+    TEC_CUDA(launch_features(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, g->or_rows, seg_off, nseg, g->seg_hist, feat_out, g->ctr,
                              g->stream));
     return TEC_OK;
 }
@@ -485,6 +563,8 @@ tec_status tec_graph_create(int64_t n_cap, int64_t nnz_cap, void *stream, tec_gr
     g->task_cap = support_task_capacity(n_cap, nnz_cap);
     if (s == TEC_OK) s = dalloc(&g->tasks, g->task_cap, "support task list");
     if (s == TEC_OK) s = dalloc(&g->flags, ntiles * (TILE / 32), "orientation bits");
+    if (s == TEC_OK) s = dalloc(&g->sym_rows, tile_rows_size(nnz_cap), "tile rows");
+    if (s == TEC_OK) s = dalloc(&g->or_rows, tile_rows_size(g->m_cap), "tile rows");
     if (s == TEC_OK) s = dalloc(&g->tile_cnt, ntiles + 1, "tile counts");
     if (s == TEC_OK) s = dalloc(&g->tile_base, ntiles + 1, "tile offsets");
     if (s == TEC_OK) s = dalloc(&g->bsum, scan_bsum_size(scan_len), "scan partials");
@@ -547,11 +627,12 @@ tec_status tec_graph_load(tec_graph *g, const void *row_off, int off_is_i64, con
     g->n = n;
     g->nnz = nnz;
     g->m = nnz / 2;
+    TEC_CUDA(launch_tile_rows(g->off, n, nnz, g->sym_rows, s));
     if (flags & TEC_VALIDATE) {
         TEC_CUDA(launch_validate(g->off, g->col, n, nnz, g->ctr, s));
         tec_status st = read_counters(g);
         if (st == TEC_OK) {
-            TEC_CUDA(launch_validate_entries(g->off, g->col, n, nnz, g->ctr, s));
+            TEC_CUDA(launch_validate_entries(g->off, g->col, n, nnz, g->sym_rows, g->ctr, s));
             st = read_counters(g);
         }
         if (st != TEC_OK) {
@@ -690,12 +771,13 @@ tec_status tec_prune(tec_graph *g, tec_measure measure, int64_t p, int64_t q, ui
     if (!g) return set_error(TEC_EINVAL, "graph is NULL");
     TEC_TRY(check_threshold((int)measure, p, q));
     DeviceGuard dg(g->device);
+    TEC_TRY(debug_refresh_caps(g));
     const uint32_t *cts = nullptr;
     int cmp = (int)measure;
     TEC_TRY(measure_counts(g, (int)measure, &cts, &cmp));
     TEC_TRY(reset_counter(g, C_KEPT));
     PruneArgs a{cmp, p, q, false};
-    TEC_CUDA(launch_prune(g->ooff, g->ocol, g->deg, cts, g->n, g->m, a, g->keep, g->parent, g->ctr, g->stream));
+    TEC_CUDA(launch_prune(g->ooff, g->ocol, g->deg, cts, g->n, g->m, g->or_rows, a, g->keep, g->parent, g->ctr, g->stream));
     g->pruned = true;
     g->hooked = false;
     g->last_measure = (int)measure;
@@ -720,9 +802,10 @@ tec_status tec_components(tec_graph *g, int32_t *labels_out, int64_t *ncomp_out)
     if (!g->pruned) return set_error(TEC_ESTATE, "tec_components needs a tec_prune first");
     if (!labels_out && g->n > 0) return set_error(TEC_EINVAL, "labels_out is NULL");
     DeviceGuard dg(g->device);
+    TEC_TRY(debug_refresh_caps(g));
     if (!g->hooked) {
         TEC_CUDA(launch_cc_init(g->parent, g->n, g->stream));
-        TEC_CUDA(launch_cc_hook(g->ooff, g->ocol, g->keep, g->n, g->m, g->parent, g->ctr, g->stream));
+        TEC_CUDA(launch_cc_hook(g->ooff, g->ocol, g->keep, g->n, g->m, g->or_rows, g->parent, g->ctr, g->stream));
         g->hooked = true;
     }
     TEC_TRY(reset_counter(g, C_NCOMP));
@@ -742,6 +825,7 @@ tec_status tec_full_pass(tec_graph *g, tec_measure measure, int64_t p, int64_t q
     TEC_TRY(check_threshold((int)measure, p, q));
     if (!labels_out && g->n > 0) return set_error(TEC_EINVAL, "labels_out is NULL");
     DeviceGuard dg(g->device);
+    TEC_TRY(debug_refresh_caps(g));
     TEC_TRY(run_full_pass(g, (int)measure, p, q, labels_out));
     if (ncomp_out) {
         TEC_TRY(read_counters(g));
@@ -760,6 +844,7 @@ tec_status tec_full_pass_host(tec_graph *g, const int64_t *row_off_host, const i
     TEC_TRY(check_threshold((int)measure, p, q));
     DeviceGuard dg(g->device);
     TEC_TRY(tec_graph_load(g, row_off_host, 1, col_host, n, nnz, TEC_HOST_PTR));
+    TEC_TRY(debug_refresh_caps(g));   // loading clears the counter block
     // Labels need their own buffer: while the finishing kernel resolves roots,
     // path compression may still re-point parent[x] at an intermediate ancestor.
     if (!g->labels) TEC_TRY(dalloc(&g->labels, g->n_cap, "label buffer"));
@@ -787,6 +872,7 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
         wide = wide || needs_wide(p[i], q[i]);
     }
     DeviceGuard dg(g->device);
+    TEC_TRY(debug_refresh_caps(g));
     const int nsl = seg_off ? nseg : 1;
     const std::vector<int> order = ascending_rows(p, q, k);
     std::vector<int64_t> hthr(2 * k);
@@ -841,6 +927,7 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
     // Rounds after a round that joined nothing return at once.
     int rounds = 2;
     while (rounds < 64 && ((int64_t)1 << (rounds - 2)) < g->n) ++rounds;
+    rounds = debug_msf_rounds(rounds);
     g->pruned = g->hooked = false;
     TEC_CUDA(launch_cc_init(g->parent, g->n, s));
     if (g->n > 0) TEC_CUDA(cudaMemsetAsync(g->best, 0, (size_t)g->n * sizeof(unsigned long long), s));
@@ -935,6 +1022,7 @@ tec_status tec_prune_components_batch(tec_graph *g, tec_measure measure, const i
     if (!p || !q || !seg_off || nseg < 1) return set_error(TEC_EINVAL, "thresholds and segment table are required");
     if (!labels_out && g->n > 0) return set_error(TEC_EINVAL, "labels_out is NULL");
     DeviceGuard dg(g->device);
+    TEC_TRY(debug_refresh_caps(g));
     if (g->sw_ncomp_cap < nseg) {
         dfree(g->sw_ncomp);
         g->sw_ncomp = nullptr;
@@ -947,7 +1035,7 @@ tec_status tec_prune_components_batch(tec_graph *g, tec_measure measure, const i
     TEC_TRY(measure_counts(g, (int)measure, &cts, &cmp));
     TEC_TRY(reset_counter(g, C_KEPT));
     TEC_CUDA(launch_cc_init(g->parent, g->n, g->stream));
-    TEC_CUDA(launch_prune_seg(g->ooff, g->ocol, g->deg, cts, g->n, g->m, cmp, p, q, seg_off, nseg, true,
+    TEC_CUDA(launch_prune_seg(g->ooff, g->ocol, g->deg, cts, g->n, g->m, g->or_rows, cmp, p, q, seg_off, nseg, true,
                               g->keep, g->parent, g->ctr, g->stream));
     g->pruned = g->hooked = true;
     TEC_CUDA(cudaMemsetAsync(g->sw_ncomp, 0, (size_t)nseg * sizeof(unsigned long long), g->stream));
@@ -968,6 +1056,18 @@ tec_status tec_set_core_staging(tec_graph *g, int enable) {
     if ((enable != 0) != g->core_enabled) {
         g->core_enabled = enable != 0;
         g->supported = g->pruned = g->hooked = false;   // counts are recomputed by the other path
+    }
+    return TEC_OK;
+}
+
+tec_status tec_set_support_tiling(tec_graph *g, int groups) {
+    clear_error();
+    if (!g) return set_error(TEC_EINVAL, "graph is NULL");
+    if (groups < -1 || groups > SUPPORT_MAX_GROUPS)
+        return set_error(TEC_EINVAL, "groups must be -1 (off), 0 (automatic) or 1..%d", SUPPORT_MAX_GROUPS);
+    if (groups != g->tile_request) {
+        g->tile_request = groups;
+        g->supported = g->pruned = g->hooked = false;   // counts are recomputed on the next use
     }
     return TEC_OK;
 }

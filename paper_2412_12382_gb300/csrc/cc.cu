@@ -18,12 +18,11 @@ __global__ void k_cc_init(int32_t *parent, int64_t n) {
 // every edge whose keep bit is set.
 __global__ void __launch_bounds__(TILE_THREADS)
 k_cc_hook(const int64_t *ooff, const int32_t *ocol, const uint32_t *keep, int64_t n, int64_t m,
-          int32_t *parent, unsigned long long *ctr) {
+          const int32_t *orows, int32_t *parent, unsigned long long *ctr) {
     if (graph_bad(ctr)) return;
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
-    const int64_t klast = min(k0 + TILE, m) - 1;
-    const int64_t r0 = row_search(ooff, 0, n - 1, k0);
-    const int64_t r1 = row_search(ooff, r0, n - 1, klast);
+    int64_t r0, r1;
+    tile_row_range(orows, ooff, n, m, r0, r1);
     for (int i = 0; i < TILE_ITEMS; ++i) {
         const int64_t j = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
         if (j >= m) break;
@@ -63,9 +62,9 @@ cudaError_t launch_cc_init(int32_t *parent, int64_t n, cudaStream_t s) {
 }
 
 cudaError_t launch_cc_hook(const int64_t *ooff, const int32_t *ocol, const uint32_t *keep, int64_t n,
-                           int64_t m, int32_t *parent, unsigned long long *ctr, cudaStream_t s) {
+                           int64_t m, const int32_t *orows, int32_t *parent, unsigned long long *ctr, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
-    k_cc_hook<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, keep, n, m, parent, ctr);
+    k_cc_hook<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, keep, n, m, orows, parent, ctr);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -44,13 +44,12 @@ __device__ __forceinline__ int seg_of(const int64_t *seg_off, int nseg, int64_t 
 
 __global__ void __launch_bounds__(TILE_THREADS)
 k_feat_hist(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t, int64_t n, int64_t m,
-            const int64_t *seg_off, int nseg, unsigned int *hist, unsigned long long *ctr) {
+            const int32_t *orows, const int64_t *seg_off, int nseg, unsigned int *hist, unsigned long long *ctr) {
     __shared__ unsigned int s_h[NBINS];
     if (graph_bad(ctr)) return;
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
-    const int64_t klast = min(k0 + TILE, m) - 1;
-    const int64_t r0 = row_search(ooff, 0, n - 1, k0);
-    const int64_t r1 = row_search(ooff, r0, n - 1, klast);
+    int64_t r0, r1;
+    tile_row_range(orows, ooff, n, m, r0, r1);
     const int s0 = seg_off ? seg_of(seg_off, nseg, r0) : 0;
     const int s1 = seg_off ? seg_of(seg_off, nseg, r1) : 0;
     const bool one = s0 == s1;                   // the common case: aggregate in shared memory
@@ -58,13 +57,28 @@ k_feat_hist(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const 
     __syncthreads();
     for (int i = 0; i < TILE_ITEMS; ++i) {
         const int64_t j = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
-        if (j >= m) break;
-        const int64_t u = row_search(ooff, r0, r1, j);
-        const int64_t s = (int64_t)deg[u] + deg[ocol[j]];
-        int64_t b = (128 * (int64_t)t[j]) / s;
-        if (b > NBINS - 1) b = NBINS - 1;
-        if (one) atomicAdd(&s_h[b], 1u);
-        else atomicAdd(&hist[(int64_t)seg_of(seg_off, nseg, u) * NBINS + b], 1u);
+        const bool valid = j < m;
+        int64_t b = -1, u = 0;
+        if (valid) {
+            u = row_search(ooff, r0, r1, j);
+            const int64_t s = (int64_t)deg[u] + deg[ocol[j]];
+            // b = floor(128 t / s): a float quotient (error far below 1)
+            // corrected by exact integer comparisons
+            const int64_t num = 128 * (int64_t)t[j];
+            b = (int64_t)((float)num / (float)s);
+            if (b * s > num) --b;
+            else if ((b + 1) * s <= num) ++b;
+            if (b > NBINS - 1) b = NBINS - 1;
+        }
+        // bin 0 (edges in no triangle, most of a sparse graph) is counted with
+        // one shared add per warp: lane-by-lane adds to one word serialise
+        const unsigned zero = __ballot_sync(0xffffffffu, valid && b == 0);
+        if (one) {
+            if (lane_id() == 0 && zero) atomicAdd(&s_h[0], (unsigned)__popc(zero));
+            if (valid && b > 0) atomicAdd(&s_h[b], 1u);
+        } else if (valid) {
+            atomicAdd(&hist[(int64_t)seg_of(seg_off, nseg, u) * NBINS + b], 1u);
+        }
     }
     __syncthreads();
     if (one && threadIdx.x < NBINS && s_h[threadIdx.x]) atomicAdd(&hist[(int64_t)s0 * NBINS + threadIdx.x], s_h[threadIdx.x]);
@@ -495,14 +509,14 @@ inline unsigned grid_for(int64_t work) {
 }  // namespace
 
 cudaError_t launch_features(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
-                            int64_t n, int64_t m, const int64_t *seg_off, int nseg, unsigned int *hist, float *feat,
-                            unsigned long long *ctr, cudaStream_t s) {
+                            int64_t n, int64_t m, const int32_t *orows, const int64_t *seg_off, int nseg,
+                            unsigned int *hist, float *feat, unsigned long long *ctr, cudaStream_t s) {
     const int ns = seg_off ? nseg : 1;
     cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)ns * NBINS * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     if (m > 0)
-        k_feat_hist<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, seg_off, ns, hist,
-                                                                         ctr);
+        k_feat_hist<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, seg_off, ns,
+                                                                         hist, ctr);
     k_feat_final<<<(unsigned)ceil_div((int64_t)ns * 32, 256), 256, 0, s>>>(hist, seg_off, ns, n, feat);
     count_launches(m > 0 ? 2 : 1);
     return cudaGetLastError();

@@ -38,14 +38,26 @@ template <bool BF16>
 __global__ void __launch_bounds__(HID) k_forward(const float *__restrict__ P, const float *__restrict__ X, int64_t B,
                                                  float *__restrict__ Z1, float *__restrict__ Z2,
                                                  float *__restrict__ Y) {
-    __shared__ float sx[IN], sh[HID], sred[HID / 32];
+    __shared__ float sx[IN], sxl[IN], sh[HID], sred[HID / 32];
     const int64_t b = blockIdx.x;
     if (b >= B) return;
     const int j = threadIdx.x;
-    for (int i = j; i < IN; i += HID) sx[i] = BF16 ? rb(X[b * IN + i]) : X[b * IN + i];
+    // bf16: each input is the sum of two bf16 values (x = hi + lo, hi = bf16(x),
+    // lo = bf16(x - hi)), so the inputs, whose rounding would otherwise move
+    // the output most, keep about 16 significant bits; weights and hidden
+    // activations are single bf16 values; products accumulate in float32
+    for (int i = j; i < IN; i += HID) {
+        const float x = X[b * IN + i];
+        sx[i] = BF16 ? rb(x) : x;
+        sxl[i] = BF16 ? rb(x - rb(x)) : 0.f;
+    }
     __syncthreads();
     float z = P[OFF_B1 + j];
-    for (int i = 0; i < IN; ++i) z += (BF16 ? rb(P[OFF_W1 + j * IN + i]) : P[OFF_W1 + j * IN + i]) * sx[i];
+    for (int i = 0; i < IN; ++i) {
+        const float w = BF16 ? rb(P[OFF_W1 + j * IN + i]) : P[OFF_W1 + j * IN + i];
+        z += w * sx[i];
+        if (BF16) z += w * sxl[i];
+    }
     if (Z1) Z1[b * HID + j] = z;
     sh[j] = BF16 ? rb(fmaxf(z, 0.f)) : fmaxf(z, 0.f);
     __syncthreads();

@@ -11,6 +11,17 @@
 namespace tec {
 namespace {
 
+// One thread per row u: the tiles whose first entry lies in u's entries
+// [off[u], off[u+1]) get u (tiles outside [0, ntiles) are skipped, so a bad
+// offset array writes nothing out of range).
+__global__ void k_tile_rows(const int64_t *off, int64_t n, int64_t ntiles, int32_t *trow) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = off[u], b = off[u + 1];
+        if (a >= b || a < 0) continue;
+        for (int64_t t = (a + TILE - 1) / TILE; t * TILE < b && t < ntiles; ++t) trow[t] = (int32_t)u;
+    }
+}
+
 __global__ void k_widen(const int32_t *in, int64_t count, int64_t *out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -36,11 +47,11 @@ __global__ void k_validate_rows(const int64_t *off, int64_t n, int64_t nnz, unsi
 // Needs valid offsets (k_validate_rows passed).  Checks ids in range, no
 // self-loop, strictly increasing rows, and that u is in N(v) for every v in N(u).
 __global__ void __launch_bounds__(TILE_THREADS)
-k_validate_entries(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz, unsigned long long *ctr) {
+k_validate_entries(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz, const int32_t *trow,
+                   unsigned long long *ctr) {
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
-    const int64_t klast = min(k0 + TILE, nnz) - 1;
-    const int64_t r0 = row_search(off, 0, n - 1, k0);
-    const int64_t r1 = row_search(off, r0, n - 1, klast);
+    int64_t r0, r1;
+    tile_row_range(trow, off, n, nnz, r0, r1);
     for (int i = 0; i < TILE_ITEMS; ++i) {
         int64_t k = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
         if (k >= nnz) break;
@@ -74,11 +85,10 @@ __device__ __forceinline__ int block_sum_int(int x) {
 // Pass 1: keep bit per symmetric entry (bit k of flags) and kept count per tile.
 __global__ void __launch_bounds__(TILE_THREADS)
 k_orient_flags(const int64_t *off, const int32_t *col, const int32_t *deg, int64_t n, int64_t nnz,
-               uint32_t *flags, int64_t *tile_cnt, unsigned long long *ctr) {
+               const int32_t *trow, uint32_t *flags, int64_t *tile_cnt, unsigned long long *ctr) {
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
-    const int64_t klast = min(k0 + TILE, nnz) - 1;
-    const int64_t r0 = row_search(off, 0, n - 1, k0);
-    const int64_t r1 = row_search(off, r0, n - 1, klast);
+    int64_t r0, r1;
+    tile_row_range(trow, off, n, nnz, r0, r1);
     int cnt = 0;
     for (int i = 0; i < TILE_ITEMS; ++i) {
         const int64_t kw = k0 + (int64_t)i * TILE_THREADS + (threadIdx.x & ~31u);
@@ -101,13 +111,13 @@ k_orient_flags(const int64_t *off, const int32_t *col, const int32_t *deg, int64
 // Pass 2: scatter kept ids to ocol[global rank of the keep bit] and write
 // ooff[u] for every row that starts (or, if empty, sits) at an entry of this tile.
 __global__ void __launch_bounds__(TILE_THREADS)
-k_orient_fill(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz, const uint32_t *flags,
-              const int64_t *tile_base, int64_t *ooff, int32_t *ocol, int64_t m, unsigned long long *ctr) {
+k_orient_fill(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz, const int32_t *trow,
+              const uint32_t *flags, const int64_t *tile_base, int64_t *ooff, int32_t *ocol, int64_t m,
+              unsigned long long *ctr) {
     __shared__ int s_wc[TILE_THREADS / 32];
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
-    const int64_t klast = min(k0 + TILE, nnz) - 1;
-    const int64_t r0 = row_search(off, 0, n - 1, k0);
-    const int64_t r1 = row_search(off, r0, n - 1, klast);
+    int64_t r0, r1;
+    tile_row_range(trow, off, n, nnz, r0, r1);
     const unsigned lane = lane_id();
     const int w = threadIdx.x >> 5;
     int64_t carry = tile_base[blockIdx.x];
@@ -165,6 +175,18 @@ inline unsigned grid_for(int64_t work, int threads, int64_t cap = 65536) {
 
 }  // namespace
 
+int64_t tile_rows_size(int64_t len) { return ceil_div(len > 0 ? len : 1, (int64_t)TILE) + 1; }
+
+cudaError_t launch_tile_rows(const int64_t *off, int64_t n, int64_t len, int32_t *trow, cudaStream_t s) {
+    if (n <= 0 || len <= 0) return cudaSuccess;
+    // every tile of a valid CSR is written; zeros keep a bad one in range
+    cudaError_t e = cudaMemsetAsync(trow, 0, (size_t)tile_rows_size(len) * sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    k_tile_rows<<<grid_for(n, 256), 256, 0, s>>>(off, n, ceil_div(len, TILE), trow);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_widen_offsets(const int32_t *in, int64_t count, int64_t *out, cudaStream_t s) {
     k_widen<<<grid_for(count, 256), 256, 0, s>>>(in, count, out);
     count_launches(1);
@@ -190,24 +212,24 @@ cudaError_t launch_validate(const int64_t *off, const int32_t *col, int64_t n, i
 }
 
 cudaError_t launch_validate_entries(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz,
-                                    unsigned long long *ctr, cudaStream_t s) {
+                                    const int32_t *trow, unsigned long long *ctr, cudaStream_t s) {
     if (nnz <= 0) return cudaSuccess;
-    k_validate_entries<<<(unsigned)ceil_div(nnz, TILE), TILE_THREADS, 0, s>>>(off, col, n, nnz, ctr);
+    k_validate_entries<<<(unsigned)ceil_div(nnz, TILE), TILE_THREADS, 0, s>>>(off, col, n, nnz, trow, ctr);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_orient(const int64_t *off, const int32_t *col, const int32_t *deg, int64_t n,
-                          int64_t nnz, uint32_t *flags, int64_t *tile_cnt, int64_t *tile_base,
+                          int64_t nnz, const int32_t *trow, uint32_t *flags, int64_t *tile_cnt, int64_t *tile_base,
                           int64_t *bsum, int64_t *ooff, int32_t *ocol, int64_t m,
                           unsigned long long *ctr, cudaStream_t s) {
     const int64_t ntiles = ceil_div(nnz, TILE);
     if (ntiles > 0) {
-        k_orient_flags<<<(unsigned)ntiles, TILE_THREADS, 0, s>>>(off, col, deg, n, nnz, flags, tile_cnt, ctr);
+        k_orient_flags<<<(unsigned)ntiles, TILE_THREADS, 0, s>>>(off, col, deg, n, nnz, trow, flags, tile_cnt, ctr);
     count_launches(1);
         cudaError_t e = scan_exclusive_i64(tile_cnt, ntiles, tile_base, bsum, s);
         if (e != cudaSuccess) return e;
-        k_orient_fill<<<(unsigned)ntiles, TILE_THREADS, 0, s>>>(off, col, n, nnz, flags, tile_base, ooff,
+        k_orient_fill<<<(unsigned)ntiles, TILE_THREADS, 0, s>>>(off, col, n, nnz, trow, flags, tile_base, ooff,
                                                                ocol, m, ctr);
         count_launches(1);
     } else {

@@ -22,14 +22,13 @@ namespace {
 template <bool HOOK, bool WIDE>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_prune(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t, int64_t n,
-        int64_t m, int measure, int64_t p, int64_t q, uint32_t *keep, int32_t *parent,
+        int64_t m, const int32_t *orows, int measure, int64_t p, int64_t q, uint32_t *keep, int32_t *parent,
         unsigned long long *ctr) {
     __shared__ int ws[TILE_THREADS / 32];
     if (graph_bad(ctr)) return;
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
-    const int64_t klast = min(k0 + TILE, m) - 1;
-    const int64_t r0 = row_search(ooff, 0, n - 1, k0);
-    const int64_t r1 = row_search(ooff, r0, n - 1, klast);
+    int64_t r0, r1;
+    tile_row_range(orows, ooff, n, m, r0, r1);
     const unsigned lane = lane_id();
     int kept = 0;
     for (int i = 0; i < TILE_ITEMS; ++i) {
@@ -61,14 +60,28 @@ k_prune(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint
 template <bool HOOK>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_prune_seg(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t, int64_t n, int64_t m,
-            int measure, const int64_t *sp, const int64_t *sq, const int64_t *seg_off, int nseg, uint32_t *keep,
-            int32_t *parent, unsigned long long *ctr) {
+            const int32_t *orows, int measure, const int64_t *sp, const int64_t *sq, const int64_t *seg_off, int nseg,
+            uint32_t *keep, int32_t *parent, unsigned long long *ctr) {
     __shared__ int ws[TILE_THREADS / 32];
     if (graph_bad(ctr)) return;
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
-    const int64_t klast = min(k0 + TILE, m) - 1;
-    const int64_t r0 = row_search(ooff, 0, n - 1, k0);
-    const int64_t r1 = row_search(ooff, r0, n - 1, klast);
+    int64_t r0, r1;
+    tile_row_range(orows, ooff, n, m, r0, r1);
+    // the segments of the tile's rows: one search per tile, and per edge only
+    // when the tile spans several graphs
+    int s0 = 0, s1 = nseg - 1;
+    while (s0 < s1) {
+        const int mid = (s0 + s1 + 1) >> 1;
+        if (seg_off[mid] <= r0) s0 = mid; else s1 = mid - 1;
+    }
+    {
+        int lo = s0, hi = nseg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (seg_off[mid] <= r1) lo = mid; else hi = mid - 1;
+        }
+        s1 = lo;
+    }
     const unsigned lane = lane_id();
     int kept = 0;
     for (int i = 0; i < TILE_ITEMS; ++i) {
@@ -77,7 +90,7 @@ k_prune_seg(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const 
         bool kp = false;
         if (j < m) {
             const int64_t u = row_search(ooff, r0, r1, j);
-            int lo = 0, hi = nseg - 1;               // segment of u
+            int lo = s0, hi = s1;                    // segment of u
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (seg_off[mid] <= u) lo = mid; else hi = mid - 1;
@@ -168,30 +181,31 @@ k_export(const int64_t *off, const int32_t *col, const int32_t *deg, const int64
 }  // namespace
 
 cudaError_t launch_prune(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
-                         int64_t n, int64_t m, PruneArgs a, uint32_t *keep, int32_t *parent,
+                         int64_t n, int64_t m, const int32_t *orows, PruneArgs a, uint32_t *keep, int32_t *parent,
                          unsigned long long *ctr, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)ceil_div(m, TILE);
     const bool wide = needs_wide(a.p, a.q);
     if (a.hook) {
-        if (wide) k_prune<true, true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, a.measure, a.p, a.q, keep, parent, ctr);
-        else k_prune<true, false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, a.measure, a.p, a.q, keep, parent, ctr);
+        if (wide) k_prune<true, true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, a.measure, a.p, a.q, keep, parent, ctr);
+        else k_prune<true, false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, a.measure, a.p, a.q, keep, parent, ctr);
     } else {
-        if (wide) k_prune<false, true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, a.measure, a.p, a.q, keep, parent, ctr);
-        else k_prune<false, false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, a.measure, a.p, a.q, keep, parent, ctr);
+        if (wide) k_prune<false, true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, a.measure, a.p, a.q, keep, parent, ctr);
+        else k_prune<false, false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, a.measure, a.p, a.q, keep, parent, ctr);
     }
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prune_seg(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
-                             int64_t n, int64_t m, int measure, const int64_t *sp, const int64_t *sq,
+                             int64_t n, int64_t m, const int32_t *orows, int measure, const int64_t *sp,
+                             const int64_t *sq,
                              const int64_t *seg_off, int nseg, bool hook, uint32_t *keep, int32_t *parent,
                              unsigned long long *ctr, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)ceil_div(m, TILE);
-    if (hook) k_prune_seg<true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, measure, sp, sq, seg_off, nseg, keep, parent, ctr);
-    else k_prune_seg<false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, measure, sp, sq, seg_off, nseg, keep, parent, ctr);
+    if (hook) k_prune_seg<true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, measure, sp, sq, seg_off, nseg, keep, parent, ctr);
+    else k_prune_seg<false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, measure, sp, sq, seg_off, nseg, keep, parent, ctr);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -35,6 +35,7 @@
 // 1024-thread block per SM for the core visits, then two 512-thread blocks per
 // SM that drain the block visits and reuse the same shared memory for warp
 // visits.
+#include <algorithm>
 #include <climits>
 
 #include "tec_internal.cuh"
@@ -60,6 +61,17 @@ constexpr int64_t CORE_MIN_WORK = 1 << 16;      // probes (about) for a small co
 constexpr int B_BATCH = 8;
 constexpr int C_BATCH = 16;                     // candidates per batch in core visits (bitmap tests are short)
 constexpr uint64_t VIS_MASK = (1ull << 32) - 1;
+// Probe-row tiling (when a range count is set): the candidates per range a
+// core centre needs to be tiled (each range's visit restages the centre's row).
+constexpr int HEAVY_CAND = 8;
+constexpr int T_BATCH = 2;                      // candidates per batch of a tiled visit (few per range)
+// Order of the core visits: 0 as emitted (about id order), 1 by d+(c)
+// descending, 2 by d+(c) ascending (a counting sort over d+ clamped to
+// ORDER_CLASSES - 1), meant to let visits running at the same time share
+// probe rows in L2.  Measured on R-MAT scale 26: 2571 ms (0), 2592 ms (1),
+// 2595 ms (2), so the visits run as emitted.
+constexpr int CORE_ORDER = 0;
+constexpr int ORDER_CLASSES = 1 << 16;
 
 __device__ __forceinline__ bool out_bit(const uint32_t *flags, int64_t e) {
     return (flags[e >> 5] >> (e & 31)) & 1u;
@@ -86,7 +98,8 @@ __device__ __forceinline__ int64_t visit_len(int64_t du, bool block) {
 // centres (core_of[c] >= 0, when core_of is given) to ctasks[]: all with
 // d+(c) > W_MAX, and smaller ones with at least CORE_MIN_WORK probes.
 __global__ void k_make_visits(const int64_t *off, const int64_t *ooff, int64_t n, uint64_t *tasks, int64_t cap,
-                              const int32_t *core_of, uint64_t *ctasks, unsigned long long *ctr) {
+                              const int32_t *core_of, uint64_t *ctasks, int groups, int32_t *heavy,
+                              int64_t heavy_cap, unsigned long long *ctr) {
     if (graph_bad(ctr)) return;
     const unsigned lane = lane_id();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -101,11 +114,26 @@ __global__ void k_make_visits(const int64_t *off, const int64_t *ooff, int64_t n
         }
         // V-mode candidates exist only if c has in-neighbours
         const int64_t ncand = du > 0 ? du + (deg > du ? deg : 0) : 0;
+        // a core centre with enough candidates per probe-row range is tiled:
+        // it goes to the heavy list and gets no visits here
+        const bool tiled = core && groups > 0 && ncand >= (int64_t)HEAVY_CAND * groups;
+        {
+            const unsigned hm = __ballot_sync(FULL, tiled);
+            unsigned long long hb = 0;
+            if (lane == 0 && hm) hb = atomicAdd(&ctr[C_NHEAVY], (unsigned long long)__popc(hm));
+            hb = __shfl_sync(FULL, hb, 0);
+            if (tiled) {
+                const int64_t slot = (int64_t)hb + __popc(hm & ((1u << lane) - 1u));
+                if (slot < heavy_cap) heavy[slot] = (int32_t)c;
+                else flag_status(ctr, ST_BADGRAPH);
+            }
+        }
+        if (tiled) core = false;
         // a core centre with little work stays a warp visit: a block visit
         // costs a few block barriers however small it is
         if (core && du <= W_MAX && ncand * du < CORE_MIN_WORK) core = false;
         const bool small = du <= W_MAX && !core;
-        const int64_t cnt = ncand > 0 ? ceil_div(ncand, visit_len(du, !small)) : 0;
+        const int64_t cnt = (ncand > 0 && !tiled) ? ceil_div(ncand, visit_len(du, !small)) : 0;
         const int64_t my_w = small ? cnt : 0, my_b = (small || core) ? 0 : cnt, my_c = core ? cnt : 0;
         int64_t sw = my_w, sb = my_b, sc = my_c;   // inclusive warp scans
 #pragma unroll
@@ -613,6 +641,8 @@ __global__ void k_reset_support_counters(unsigned long long *ctr) {
     ctr[C_NEXTW] = 0;
     ctr[C_NCTASK] = 0;
     ctr[C_NEXTC] = 0;
+    ctr[C_NHEAVY] = 0;
+    ctr[C_NEXTT] = 0;
 }
 
 // ------------------------------------------------------------------ core labels
@@ -776,6 +806,211 @@ k_support_core(const int64_t *off, const int32_t *col, const uint32_t *flags, co
     }
 }
 
+// ------------------------------------------------------------------ core visit order
+
+__device__ __forceinline__ int order_class(const int64_t *ooff, uint64_t task) {
+    const int32_t c = (int32_t)(task >> 32);
+    const int64_t d = min(ooff[c + 1] - ooff[c], (int64_t)ORDER_CLASSES - 1);
+    return CORE_ORDER == 1 ? ORDER_CLASSES - 1 - (int)d : (int)d;
+}
+
+__global__ void k_order_count(const uint64_t *ctasks, const int64_t *ooff, unsigned long long *hist,
+                              const unsigned long long *ctr) {
+    const int64_t nt = (int64_t)ctr[C_NCTASK];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&hist[order_class(ooff, ctasks[i])], 1ull);
+}
+
+// out[base[class] + cursor]: the visits grouped by class, classes ascending.
+__global__ void k_order_fill(const uint64_t *ctasks, const int64_t *ooff, const int64_t *base,
+                             unsigned long long *cursor, uint64_t *out, int64_t cap, unsigned long long *ctr) {
+    const int64_t nt = (int64_t)ctr[C_NCTASK];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t task = ctasks[i];
+        const int cls = order_class(ooff, task);
+        const int64_t pos = base[cls] + (int64_t)atomicAdd(&cursor[cls], 1ull);
+        if (pos < cap) out[pos] = task;
+        else flag_status(ctr, ST_BADGRAPH);
+    }
+}
+
+// ------------------------------------------------------------------ probe-row tiling
+//
+// The core kernel above reads a centre's candidate rows wherever they lie, so
+// every probe row is fetched from DRAM once per centre probing it, and every
+// third-edge credit is a random read-modify-write of a DRAM-resident counter.
+// The tiled kernel visits a heavy centre once per vertex-id range ("group")
+// of about equal probe-id volume (set by tec_set_support_tiling), all visits of group 0
+// first: the centres visited at the same time probe only the rows of one
+// group, which stay in L2 with their counters.  A visit covers the candidates
+// of one group, which are a contiguous slice of the centre's oriented row
+// (U-mode) and of its symmetric row (V-mode), both sorted by id.  The counts
+// do not change: every oriented edge is still intersected exactly once, from
+// the same side.
+
+// gb[g] = first vertex of group g: the smallest v with ooff[v] >= g m / groups
+// (gb[0] = 0, gb[groups] = n).
+__global__ void k_tile_groups(const int64_t *ooff, int64_t n, int64_t m, int groups, int32_t *gb) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g > groups) return;
+    if (g == 0 || g == groups) {
+        gb[g] = g == 0 ? 0 : (int32_t)n;
+        return;
+    }
+    const int64_t target = (int64_t)((__int128)m * g / groups);
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (ooff[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    gb[g] = (int32_t)lo;
+}
+
+// One warp per tiled centre h: bu[g * hcap + h] = first position of N+(c)
+// holding an id >= gb[g], bv[...] the same in c's symmetric row (g = 0..groups).
+__global__ void k_tile_bounds(const int64_t *off, const int32_t *col, const int64_t *ooff, const int32_t *ocol,
+                              const int32_t *heavy, int64_t hcap, int groups, const int32_t *gb, int32_t *bu,
+                              int32_t *bv, const unsigned long long *ctr) {
+    const int64_t H = (int64_t)ctr[C_NHEAVY];
+    const int64_t warps = (int64_t)gridDim.x * blockDim.x / 32;
+    for (int64_t h = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; h < H && h < hcap; h += warps) {
+        const int32_t c = heavy[h];
+        const int64_t cb = ooff[c], ce = ooff[c + 1], sb = off[c], se = off[c + 1];
+        for (int g = (int)lane_id(); g <= groups; g += 32) {
+            const int32_t x = gb[g];
+            bu[(int64_t)g * hcap + h] = (int32_t)(lower_bound_g(ocol, cb, ce, x) - cb);
+            bv[(int64_t)g * hcap + h] = (int32_t)(lower_bound_g(col, sb, se, x) - sb);
+        }
+    }
+}
+
+__device__ __forceinline__ bool tile_item_nonempty(const int32_t *bu, const int32_t *bv, int64_t hcap, int g,
+                                                   int64_t h) {
+    const int64_t a = (int64_t)g * hcap + h, b = a + hcap;
+    return bu[b] > bu[a] || bv[b] > bv[a];
+}
+
+// icnt[g] = number of tiled centres with candidates in group g.  Grid: x over
+// centres, y over groups.
+__global__ void k_tile_count(const int32_t *bu, const int32_t *bv, int64_t hcap, int groups, int64_t *icnt,
+                             const unsigned long long *ctr) {
+    const int64_t H = min((int64_t)ctr[C_NHEAVY], hcap);
+    for (int g = blockIdx.y; g < groups; g += gridDim.y) {
+        int c = 0;
+        for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < H; h += (int64_t)gridDim.x * blockDim.x)
+            c += tile_item_nonempty(bu, bv, hcap, g, h) ? 1 : 0;
+        c = warp_sum(c);
+        if (lane_id() == 0 && c) atomicAdd((unsigned long long *)&icnt[g], (unsigned long long)c);
+    }
+}
+
+// Writes the items of group g at ioff[g] + (a per-group cursor), range-major.
+__global__ void k_tile_fill(const int32_t *bu, const int32_t *bv, int64_t hcap, int groups, const int64_t *ioff,
+                            int64_t *cursor, uint32_t *items, int64_t item_cap, unsigned long long *ctr) {
+    const int64_t H = min((int64_t)ctr[C_NHEAVY], hcap);
+    const unsigned lane = lane_id();
+    for (int g = blockIdx.y; g < groups; g += gridDim.y) {
+        for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < H; base += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t h = base + threadIdx.x;
+            const bool ne = h < H && tile_item_nonempty(bu, bv, hcap, g, h);
+            const unsigned bm = __ballot_sync(FULL, ne);
+            unsigned long long at = 0;
+            if (lane == 0 && bm) at = atomicAdd((unsigned long long *)&cursor[g], (unsigned long long)__popc(bm));
+            at = __shfl_sync(FULL, at, 0);
+            if (ne) {
+                const int64_t slot = ioff[g] + (int64_t)at + __popc(bm & ((1u << lane) - 1u));
+                if (slot < item_cap) items[slot] = ((uint32_t)g << CORE_BITS) | (uint32_t)h;
+                else flag_status(ctr, ST_BADGRAPH);
+            }
+        }
+    }
+}
+
+// Persistent kernel, one 1024-thread block per SM: the tiled items in order.
+// Per item (group g, centre c): per chunk of N+(c), stage the bitmap as the
+// core kernel does, run the batches of the group's U-mode slice [u0, u1) and
+// V-mode slice [v0, v1) of the candidates, flush the centre's counters and
+// clear the bits.
+__global__ void __launch_bounds__(C_THREADS, 1)
+k_support_tiled(const int64_t *off, const int32_t *col, const uint32_t *flags, const int64_t *ooff,
+                const int32_t *ocol, const int32_t *pv2, const int32_t *core_of, uint32_t *t, const int32_t *heavy,
+                int64_t hcap, const int32_t *bu, const int32_t *bv, const uint32_t *items, const int64_t *ioff,
+                int groups, unsigned long long *ctr) {
+    extern __shared__ unsigned long long csm[];
+    unsigned long long *bm = csm;                                           // C_WORDS
+    uint16_t *pref = reinterpret_cast<uint16_t *>(bm + C_WORDS);            // C_WORDS
+    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(pref + C_WORDS);         // C_CHUNK
+    __shared__ CoreScratch s_cws[C_WARPS];
+    __shared__ long long s_item;
+    __shared__ int s_next;
+    if (graph_bad(ctr)) return;
+    const unsigned lane = lane_id();
+    CoreScratch &ws = s_cws[threadIdx.x >> 5];
+    for (int i = threadIdx.x; i < C_WORDS; i += C_THREADS) bm[i] = 0ull;
+    for (int i = threadIdx.x; i < C_CHUNK; i += C_THREADS) s_cnt[i] = 0u;
+    __syncthreads();
+    const int64_t nitems = ioff[groups];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(&ctr[C_NEXTT], 1ull);
+        __syncthreads();
+        const int64_t it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const uint32_t code = items[it];
+        const int g = (int)(code >> CORE_BITS);
+        const int64_t h = (int64_t)(code & (uint32_t)(CORE_CAP - 1));
+        const int32_t c = heavy[h];
+        const int64_t cb = ooff[c];
+        const int64_t du = ooff[c + 1] - cb;
+        const int64_t a = (int64_t)g * hcap + h;
+        const int64_t u0 = bu[a], u1 = bu[a + hcap], v0 = bv[a], v1 = bv[a + hcap];
+        const int64_t nbu = ceil_div(u1 - u0, (int64_t)T_BATCH), nb = nbu + ceil_div(v1 - v0, (int64_t)T_BATCH);
+        const bool chunked = du > C_CHUNK;
+        const int32_t cval = core_of[c];
+        for (int64_t c0 = 0; c0 < du; c0 += C_CHUNK) {
+            const int cl = (int)min((int64_t)C_CHUNK, du - c0);
+            for (int i = threadIdx.x; i < cl; i += C_THREADS) {
+                const int32_t w = pv2[cb + c0 + i];
+                if (w >= 0) atomicOr(&bm[w >> 6], 1ull << (w & 63));
+                else flag_status(ctr, ST_BADGRAPH);   // a core centre has only core out-neighbours
+            }
+            if (threadIdx.x == 0) s_next = 0;
+            __syncthreads();
+            for (int i = threadIdx.x; i < cl; i += C_THREADS) {
+                const int32_t w = pv2[cb + c0 + i];
+                if (w >= 0 && !(i > 0 && (pv2[cb + c0 + i - 1] >> 6) == (w >> 6)))   // the word's first member
+                    pref[w >> 6] = (uint16_t)i;
+            }
+            __syncthreads();
+            const CoreSet S{bm, pref, s_cnt};
+            const int32_t lo_id = ocol[cb + c0], hi_id = ocol[cb + c0 + cl - 1];
+            for (;;) {
+                int b = 0;
+                if (lane == 0) b = atomicAdd(&s_next, 1);
+                b = __shfl_sync(FULL, b, 0);
+                if (b >= nb) break;
+                // batch b: of the U-mode slice first, then of the V-mode slice
+                // (candidate q >= du is entry q - du of the symmetric row)
+                const int64_t q0 = b < nbu ? u0 + (int64_t)b * T_BATCH : du + v0 + (int64_t)(b - nbu) * T_BATCH;
+                const int64_t qe = b < nbu ? u1 : du + v1;
+                process_batch(off, col, flags, ooff, ocol, pv2, t, c, cval, cb, du, q0, min(qe, q0 + T_BATCH),
+                              chunked, lo_id, hi_id, S, s_cnt, false, ws, ctr);
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < cl; i += C_THREADS) {
+                const uint32_t cv = s_cnt[i];
+                if (cv) {
+                    atomicAdd(&t[cb + c0 + i], cv);
+                    s_cnt[i] = 0u;
+                }
+                const int32_t w = pv2[cb + c0 + i];
+                if (w >= 0) bm[w >> 6] = 0ull;
+            }
+            __syncthreads();
+        }
+    }
+}
+
 }  // namespace
 
 int64_t support_task_capacity(int64_t n, int64_t nnz) {
@@ -805,10 +1040,34 @@ cudaError_t launch_core_labels(const int32_t *deg, int64_t n, const int32_t *oco
     return cudaGetLastError();
 }
 
+int64_t core_order_classes() { return CORE_ORDER != 0 ? ORDER_CLASSES : 0; }
+
+// Measured on R-MAT scale 26 (1 GB300): 2.57 s untiled against 3.0-18 s for
+// every tiled setting tried (8..248 ranges, 1..16 candidates per batch, 8 or
+// 64 candidates per range): the per-visit start-up (dependent loads of the
+// item, the centre and its first rows, and the block barriers) outweighs
+// the L2 reuse.  So the automatic rule leaves tiling off; a range count set
+// with tec_set_support_tiling still runs it.
+int support_auto_groups(int64_t m) {
+    (void)m;
+    return 0;
+}
+
+int64_t support_heavy_capacity(int64_t n) { return std::max<int64_t>(1, std::min<int64_t>(n, CORE_CAP)); }
+
+int64_t support_item_capacity(int64_t nnz, int groups, int64_t heavy_cap) {
+    // a tiled centre has ncand >= HEAVY_CAND * groups candidates and
+    // sum(ncand) <= m + nnz, so items <= heavy * groups <= 1.5 nnz / HEAVY_CAND
+    if (groups <= 0) return 0;
+    const int64_t by_cand = (nnz + nnz / 2) / HEAVY_CAND + 1;
+    return std::max<int64_t>(1, std::min<int64_t>(heavy_cap * groups, by_cand));
+}
+
 cudaError_t launch_support(const int64_t *off, const int32_t *col, const uint32_t *flags, const int64_t *ooff,
                            const int32_t *ocol, int64_t n, int64_t m, uint32_t *t, uint64_t *tasks,
                            int64_t task_cap, unsigned long long *ctr, int num_sms, cudaStream_t s,
-                           const int32_t *pv2, const int32_t *core_of, uint64_t *ctasks) {
+                           const int32_t *pv2, const int32_t *core_of, uint64_t *ctasks,
+                           const SupportTiling &tl, const CoreOrder &order) {
     if (m > 0) {
         cudaError_t e = cudaMemsetAsync(t, 0, (size_t)m * sizeof(uint32_t), s);
         if (e != cudaSuccess) return e;
@@ -818,20 +1077,58 @@ cudaError_t launch_support(const int64_t *off, const int32_t *col, const uint32_
     cudaError_t e = cudaFuncSetAttribute(k_support, cudaFuncAttributeMaxDynamicSharedMemorySize, bsmem);
     if (e != cudaSuccess) return e;
     const bool core = pv2 && core_of && ctasks;
+    const int groups = (core && tl.groups > 0 && tl.items) ? tl.groups : 0;
     if (core) {
         e = cudaFuncSetAttribute(k_support_core, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_SMEM);
+        if (e != cudaSuccess) return e;
+    }
+    if (groups) {
+        e = cudaFuncSetAttribute(k_support_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C_SMEM);
         if (e != cudaSuccess) return e;
     }
     k_reset_support_counters<<<1, 1, 0, s>>>(ctr);
     {
         const int64_t g = ceil_div(n, 256);
-        k_make_visits<<<(unsigned)(g < 65536 ? g : 65536), 256, 0, s>>>(off, ooff, n, tasks, task_cap,
-                                                                        core ? core_of : nullptr, ctasks, ctr);
+        k_make_visits<<<(unsigned)(g < 65536 ? g : 65536), 256, 0, s>>>(
+            off, ooff, n, tasks, task_cap, core ? core_of : nullptr, ctasks, groups, tl.heavy, tl.heavy_cap, ctr);
     }
     int launched = 2;
+    if (groups) {
+        k_tile_groups<<<(unsigned)ceil_div(groups + 1, 256), 256, 0, s>>>(ooff, n, m, groups, tl.gb);
+        const int64_t hw = ceil_div(tl.heavy_cap, 8);    // 8 warps of 256-thread blocks
+        k_tile_bounds<<<(unsigned)std::min<int64_t>(std::max<int64_t>(hw, 1), 8192), 256, 0, s>>>(
+            off, col, ooff, ocol, tl.heavy, tl.heavy_cap, groups, tl.gb, tl.bu, tl.bv, ctr);
+        if ((e = cudaMemsetAsync(tl.icnt, 0, (size_t)(groups + 1) * sizeof(int64_t), s)) != cudaSuccess) return e;
+        const unsigned hx = (unsigned)std::min<int64_t>(std::max<int64_t>(ceil_div(tl.heavy_cap, 256), 1), 64);
+        const dim3 grid(hx, (unsigned)std::min(groups, 1024));
+        k_tile_count<<<grid, 256, 0, s>>>(tl.bu, tl.bv, tl.heavy_cap, groups, tl.icnt, ctr);
+        if ((e = scan_exclusive_i64(tl.icnt, groups, tl.ioff, tl.bsum, s)) != cudaSuccess) return e;
+        // the counts are reused as the fill cursors
+        if ((e = cudaMemsetAsync(tl.icnt, 0, (size_t)(groups + 1) * sizeof(int64_t), s)) != cudaSuccess) return e;
+        k_tile_fill<<<grid, 256, 0, s>>>(tl.bu, tl.bv, tl.heavy_cap, groups, tl.ioff, tl.icnt, tl.items, tl.item_cap,
+                                         ctr);
+        k_support_tiled<<<(unsigned)num_sms, C_THREADS, C_SMEM, s>>>(off, col, flags, ooff, ocol, pv2, core_of, t,
+                                                                     tl.heavy, tl.heavy_cap, tl.bu, tl.bv, tl.items,
+                                                                     tl.ioff, groups, ctr);
+        launched += 5;
+    }
     if (core) {
+        const uint64_t *cl = ctasks;
+        if (CORE_ORDER != 0 && order.sorted) {
+            const size_t hb = (size_t)(ORDER_CLASSES + 1) * sizeof(int64_t);
+            if ((e = cudaMemsetAsync(order.hist, 0, hb, s)) != cudaSuccess) return e;
+            const unsigned og = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(task_cap, 256), 4096));
+            k_order_count<<<og, 256, 0, s>>>(ctasks, ooff, (unsigned long long *)order.hist, ctr);
+            if ((e = scan_exclusive_i64(order.hist, ORDER_CLASSES, order.base, order.bsum, s)) != cudaSuccess)
+                return e;
+            if ((e = cudaMemsetAsync(order.hist, 0, hb, s)) != cudaSuccess) return e;
+            k_order_fill<<<og, 256, 0, s>>>(ctasks, ooff, order.base, (unsigned long long *)order.hist, order.sorted,
+                                            task_cap, ctr);
+            cl = order.sorted;
+            launched += 2;
+        }
         k_support_core<<<(unsigned)num_sms, C_THREADS, C_SMEM, s>>>(off, col, flags, ooff, ocol, pv2, core_of, t,
-                                                                    ctasks, ctr);
+                                                                    cl, ctr);
         ++launched;
     }
     k_support<<<(unsigned)(num_sms * 2), B_THREADS, bsmem, s>>>(off, col, flags, ooff, ocol, t, tasks, task_cap, ctr);

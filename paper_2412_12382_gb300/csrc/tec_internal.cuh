@@ -36,6 +36,9 @@ enum Ctr : int {
     C_CHANGED = 7,
     C_NCTASK = 8,       // core block visits
     C_NEXTC = 9,        // next core block visit
+    C_NHEAVY = 10,      // core centres whose candidates are tiled by probe-row group
+    C_NEXTT = 11,       // next tiled (group, centre) item
+    C_DEBUG_LINK_CAP = 12,  // debug builds: 1 + a lowered union-find retry cap (0: the normal cap)
     C_COUNT = 16
 };
 
@@ -86,14 +89,18 @@ cudaError_t scan_exclusive_i32(const int32_t *in, int64_t N, int64_t *out, int64
 int64_t scan_bsum_size(int64_t N);
 
 // orient.cu
+// trow[t] = the row of entry t * TILE (the last r with off[r] <= t * TILE) for
+// the ceil(len / TILE) tiles of a CSR with n rows and len entries.
+cudaError_t launch_tile_rows(const int64_t *off, int64_t n, int64_t len, int32_t *trow, cudaStream_t s);
+int64_t tile_rows_size(int64_t len);
 cudaError_t launch_widen_offsets(const int32_t *in, int64_t count, int64_t *out, cudaStream_t s);
 cudaError_t launch_degrees(const int64_t *off, int64_t n, int32_t *deg, cudaStream_t s);
 cudaError_t launch_validate(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz,
                             unsigned long long *ctr, cudaStream_t s);
 cudaError_t launch_validate_entries(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz,
-                                    unsigned long long *ctr, cudaStream_t s);
+                                    const int32_t *trow, unsigned long long *ctr, cudaStream_t s);
 cudaError_t launch_orient(const int64_t *off, const int32_t *col, const int32_t *deg, int64_t n,
-                          int64_t nnz, uint32_t *flags, int64_t *tile_cnt, int64_t *tile_base,
+                          int64_t nnz, const int32_t *trow, uint32_t *flags, int64_t *tile_cnt, int64_t *tile_base,
                           int64_t *bsum, int64_t *ooff, int32_t *ocol, int64_t m,
                           unsigned long long *ctr, cudaStream_t s);
 
@@ -107,12 +114,50 @@ int64_t support_task_capacity(int64_t n, int64_t nnz);
 cudaError_t launch_core_labels(const int32_t *deg, int64_t n, const int32_t *ocol, int64_t m,
                                unsigned long long *hist, long long *meta, int64_t *tcnt, int64_t *tbase,
                                int64_t *bsum, int32_t *core_of, int32_t *pv2, cudaStream_t s);
+// Probe-row tiling of the core centres with the most candidates (support.cu):
+// the vertex ids are split into `groups` ranges of about equal oriented-row
+// volume, and each such centre is visited once per range that holds some of
+// its candidates, all visits of range 0 first, then range 1, ...  The probe
+// rows and counters of one range fit in L2, so centres visited at the same
+// time share them.  groups = 0: no tiling.
+struct SupportTiling {
+    int groups = 0;
+    int32_t *gb = nullptr;          // groups + 1 range starts (vertex ids)
+    int32_t *heavy = nullptr;       // heavy_cap tiled centres
+    int64_t heavy_cap = 0;
+    int32_t *bu = nullptr;          // (groups + 1) x heavy_cap: first position of each range in N+(c)
+    int32_t *bv = nullptr;          // (groups + 1) x heavy_cap: first position of each range in N(c)
+    uint32_t *items = nullptr;      // item_cap (range << 20 | heavy index) items, range-major
+    int64_t item_cap = 0;
+    int64_t *icnt = nullptr;        // groups + 1 items per range, then their prefix (groups + 1)
+    int64_t *ioff = nullptr;
+    int64_t *bsum = nullptr;        // scan scratch for groups entries
+};
+// Buffers of the d+ order of the core visits: ORDER_CLASSES + 1 counts and
+// offsets, scan scratch, and the reordered visit list (task_cap entries).
+struct CoreOrder {
+    int64_t *hist = nullptr;
+    int64_t *base = nullptr;
+    int64_t *bsum = nullptr;
+    uint64_t *sorted = nullptr;
+};
+int64_t core_order_classes();
+// Ranges the automatic rule gives a graph of m oriented edges (0: no tiling).
+int support_auto_groups(int64_t m);
+// Largest number of ranges, and the buffer sizes for a graph of n vertices,
+// nnz symmetric entries and `groups` ranges.
+constexpr int SUPPORT_MAX_GROUPS = 4095;
+int64_t support_heavy_capacity(int64_t n);
+int64_t support_item_capacity(int64_t nnz, int groups, int64_t heavy_cap);
+
 // Triangle counts; with pv2 / core_of / ctasks (capacity task_cap) block
-// visits of core centres run in the bitmap kernel.
+// visits of core centres run in the bitmap kernel, and with tiling.groups > 0
+// (which needs the core staging) the heaviest core centres are tiled.
 cudaError_t launch_support(const int64_t *off, const int32_t *col, const uint32_t *flags, const int64_t *ooff,
                            const int32_t *ocol, int64_t n, int64_t m, uint32_t *t, uint64_t *tasks,
                            int64_t task_cap, unsigned long long *ctr, int num_sms, cudaStream_t s,
-                           const int32_t *pv2, const int32_t *core_of, uint64_t *ctasks);
+                           const int32_t *pv2, const int32_t *core_of, uint64_t *ctasks,
+                           const SupportTiling &tiling, const CoreOrder &order);
 
 // prune.cu
 struct PruneArgs {
@@ -120,13 +165,14 @@ struct PruneArgs {
     int64_t p, q;
     bool hook;          // also union the endpoints of every kept edge into `parent`
 };
+// orows: the tile-row table of the oriented CSR (or nullptr).
 cudaError_t launch_prune(const int64_t *ooff, const int32_t *ocol, const int32_t *deg,
-                         const uint32_t *t, int64_t n, int64_t m, PruneArgs a, uint32_t *keep,
+                         const uint32_t *t, int64_t n, int64_t m, const int32_t *orows, PruneArgs a, uint32_t *keep,
                          int32_t *parent, unsigned long long *ctr, cudaStream_t s);
 cudaError_t launch_prune_seg(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
-                             int64_t n, int64_t m, int measure, const int64_t *sp, const int64_t *sq,
-                             const int64_t *seg_off, int nseg, bool hook, uint32_t *keep, int32_t *parent,
-                             unsigned long long *ctr, cudaStream_t s);
+                             int64_t n, int64_t m, const int32_t *orows, int measure, const int64_t *sp,
+                             const int64_t *sq, const int64_t *seg_off, int nseg, bool hook, uint32_t *keep,
+                             int32_t *parent, unsigned long long *ctr, cudaStream_t s);
 cudaError_t launch_export(const int64_t *off, const int32_t *col, const int32_t *deg,
                           const int64_t *ooff, const int32_t *ocol, const uint32_t *t,
                           const uint32_t *keep, int64_t n, int64_t nnz, const int64_t *uoff,
@@ -174,8 +220,8 @@ cudaError_t launch_snapshot(int32_t *parent, int64_t n, int32_t *labels, const i
 
 // eval.cu: picker features per graph and adjusted Rand index per (level, graph).
 cudaError_t launch_features(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
-                            int64_t n, int64_t m, const int64_t *seg_off, int nseg, unsigned int *hist, float *feat,
-                            unsigned long long *ctr, cudaStream_t s);
+                            int64_t n, int64_t m, const int32_t *orows, const int64_t *seg_off, int nseg,
+                            unsigned int *hist, float *feat, unsigned long long *ctr, cudaStream_t s);
 int ari_table_bits(int64_t n);
 cudaError_t launch_best_level(const double *ari, int k, int nseg, int32_t *best, double *best_ari, cudaStream_t s);
 // ARI_CHUNK levels share one zeroing of the pair sums (sums holds 2 x nseg x ARI_CHUNK).
@@ -218,7 +264,7 @@ cudaError_t launch_prf(const int32_t *labels, int k, const int32_t *truth, int64
 // cc.cu
 cudaError_t launch_cc_init(int32_t *parent, int64_t n, cudaStream_t s);
 cudaError_t launch_cc_hook(const int64_t *ooff, const int32_t *ocol, const uint32_t *keep,
-                           int64_t n, int64_t m, int32_t *parent, unsigned long long *ctr,
+                           int64_t n, int64_t m, const int32_t *orows, int32_t *parent, unsigned long long *ctr,
                            cudaStream_t s);
 cudaError_t launch_cc_finish(int32_t *parent, int64_t n, int32_t *labels,
                              unsigned long long *ctr, cudaStream_t s);
@@ -291,6 +337,25 @@ __device__ __forceinline__ int64_t row_search(const int64_t *off, int64_t lo, in
     return lo;
 }
 
+// Rows of tile blockIdx.x (entries [blockIdx.x * TILE, + TILE) of a CSR with
+// `len` entries): r0 = the row of its first entry, r1 >= the row of its last.
+// From the tile-row table trow of launch_tile_rows when given (two loads),
+// else by binary search over all n rows.
+__device__ __forceinline__ void tile_row_range(const int32_t *trow, const int64_t *off, int64_t n, int64_t len,
+                                               int64_t &r0, int64_t &r1) {
+    const int64_t k0 = (int64_t)blockIdx.x * TILE;
+    if (trow) {
+        r0 = trow[blockIdx.x];
+        r1 = k0 + TILE < len ? (int64_t)trow[blockIdx.x + 1] : n - 1;
+        r0 = r0 < 0 ? 0 : (r0 > n - 1 ? n - 1 : r0);      // in range even for a bad CSR
+        r1 = r1 < r0 ? r0 : (r1 > n - 1 ? n - 1 : r1);
+    } else {
+        const int64_t klast = (k0 + TILE < len ? k0 + TILE : len) - 1;
+        r0 = row_search(off, 0, n - 1, k0);
+        r1 = row_search(off, r0, n - 1, klast);
+    }
+}
+
 // Orientation order: u before v iff (deg u, u) < (deg v, v).
 __device__ __forceinline__ bool rank_less(int32_t du, int64_t u, int32_t dv, int64_t v) {
     return du < dv || (du == dv && u < v);
@@ -361,6 +426,8 @@ struct tec_graph {
     uint64_t *tasks = nullptr;      // support work list
     int64_t task_cap = 0;
     uint32_t *flags = nullptr;
+    int32_t *sym_rows = nullptr;    // tile-row table of the symmetric CSR
+    int32_t *or_rows = nullptr;     // tile-row table of the oriented CSR
     int64_t *tile_cnt = nullptr;
     int64_t *tile_base = nullptr;
     int64_t *bsum = nullptr;
@@ -378,10 +445,15 @@ struct tec_graph {
     int32_t *core_of = nullptr;           // n: core code or -1
     int32_t *pv2 = nullptr;               // m + 4: core codes of ocol
     uint64_t *ctasks = nullptr;           // task_cap core block visits
+    tec::CoreOrder corder;                // the core visits reordered by out-degree (optional)
     int64_t *core_tc = nullptr;           // 2 x ceil(n_cap / TILE) + 64: tile counts and bases
     unsigned long long *core_hist = nullptr;  // 33 degree bins + 2 meta words
     int core_state = 0;                   // 0 untried, 1 available, -1 unavailable
     bool core_enabled = true;             // tec_set_core_staging
+    // probe-row tiling of the heaviest core centres (buffers for tile.groups ranges)
+    tec::SupportTiling tile;
+    int tile_request = 0;                 // tec_set_support_tiling: 0 automatic, -1 off, > 0 ranges
+    int tile_failed_groups = 0;           // range count whose buffers could not be allocated
     // K4 participation per oriented edge (saturating), allocated on first use
     uint32_t *k4 = nullptr;
     unsigned long long *k4_next = nullptr;

@@ -28,12 +28,26 @@ __device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x) {
     return uf_find_from(parent, x, __ldcg(&parent[x]));
 }
 
+// Retry cap of one link.  Debug builds read a lowered cap from the counter
+// block (set from TEC_DEBUG_LINK_CAP by the host), so a test can make the cap
+// run out on purpose; 0 there means the normal cap.
+__device__ __forceinline__ int link_cap(const unsigned long long *ctr) {
+#ifdef TEC_DEBUG
+    const unsigned long long c = ctr[C_DEBUG_LINK_CAP];
+    return c ? (int)(c - 1) : LINK_RETRY_CAP;
+#else
+    (void)ctr;
+    return LINK_RETRY_CAP;
+#endif
+}
+
 // Each failed compare-and-swap means a root was hooked by another thread, so
 // the retry loop makes global progress; the cap only guards against a broken
 // forest and reports TEC_ETIMEOUT.
 __device__ __forceinline__ void uf_link(int32_t *parent, int32_t a, int32_t b, unsigned long long *ctr) {
     int32_t ra = uf_find(parent, a), rb = uf_find(parent, b);
-    for (int it = 0; it < LINK_RETRY_CAP; ++it) {
+    const int cap = link_cap(ctr);
+    for (int it = 0; it < cap; ++it) {
         if (ra == rb) return;
         const int32_t hi = ra > rb ? ra : rb;
         const int32_t lo = ra > rb ? rb : ra;
@@ -53,7 +67,8 @@ namespace tec {
 // (exactly one caller succeeds for each merge).
 __device__ __forceinline__ bool uf_link_merged(int32_t *parent, int32_t a, int32_t b, unsigned long long *ctr) {
     int32_t ra = uf_find(parent, a), rb = uf_find(parent, b);
-    for (int it = 0; it < LINK_RETRY_CAP; ++it) {
+    const int cap = link_cap(ctr);
+    for (int it = 0; it < cap; ++it) {
         if (ra == rb) return false;
         const int32_t hi = ra > rb ? ra : rb;
         const int32_t lo = ra > rb ? rb : ra;

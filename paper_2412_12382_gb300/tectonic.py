@@ -84,6 +84,7 @@ SIGNATURES = {
     "tec_sweep_stats": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "tec_rule_of_thumb": ([_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
     "tec_set_core_staging": ([_P, ctypes.c_int], ctypes.c_int),
+    "tec_set_support_tiling": ([_P, ctypes.c_int], ctypes.c_int),
     "tec_edge_k4": ([_P, _P], ctypes.c_int),
     "tec_prf": ([_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
     "tec_components_noalloc": ([_I64, _I64, _P, _P, _P, _P, _PI64, _P], ctypes.c_int),
@@ -347,6 +348,10 @@ class Graph:
         check(self._lib.tec_ari(self._h, k, _ptr(labels.contiguous()), _ptr(truth.contiguous()),
                                 _ptr(seg_off) if seg_off is not None else None, nseg, _ptr(out)))
         return out
+
+    def set_support_tiling(self, groups: int):
+        """Probe-row tiling of the triangle counts: -1 off, 0 automatic, k > 0 that many ranges."""
+        check(self._lib.tec_set_support_tiling(self._h, int(groups)))
 
     def set_core_staging(self, enable: bool):
         """Exact bitmap staging of high-degree centres in the triangle counts (default on)."""

@@ -27,7 +27,7 @@
 int main(int argc, char **argv) {
     FILE *f;
     int64_t n = 0, nnz = 0, *off = NULL, *dp = NULL, *dq = NULL, hp[2], hq[2], kept = -1, ncomp = -1;
-    int32_t *col = NULL;
+    int32_t *col = NULL, *labels = NULL;
     size_t meta_len = 0;
     char *meta = NULL;
     tec_graph *g = NULL;
@@ -60,7 +60,8 @@ int main(int argc, char **argv) {
     CHECK(cudaMemcpy(hq, dq, sizeof hq, cudaMemcpyDeviceToHost) == cudaSuccess);
     CHECK(hp[0] >= 1 && hp[0] <= 64 && hq[0] == 128 && hp[1] >= 1 && hp[1] <= 64 && hq[1] == 128);
     CHECK(tec_prune(g, TEC_TECTONIC, hp[0], hq[0], NULL, &kept) == TEC_OK);
-    CHECK(tec_components(g, NULL, &ncomp) == TEC_OK);
+    CHECK(cudaMalloc((void **)&labels, (size_t)n * sizeof(int32_t)) == cudaSuccess);
+    CHECK(tec_components(g, labels, &ncomp) == TEC_OK);
     CHECK(tec_picker_save(pk, argv[3], meta) == TEC_OK);
     printf("%lld %lld %lld %lld %lld %lld\n", (long long)hp[0], (long long)hq[0], (long long)hp[1], (long long)hq[1],
            (long long)kept, (long long)ncomp);
@@ -68,6 +69,7 @@ int main(int argc, char **argv) {
     CHECK(tec_graph_free(g) == TEC_OK);
     cudaFree(dp);
     cudaFree(dq);
+    cudaFree(labels);
     free(off);
     free(col);
     free(meta);

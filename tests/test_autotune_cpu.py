@@ -15,8 +15,11 @@ def test_every_tunable_has_one_definition_and_safe_candidates():
     for name, (fname, cands) in A.TUNABLES.items():
         text = open(os.path.join(B.CSRC, fname)).read()
         v = A.int_value(A.current_value(text, name))
+        if name == "CORE_ORDER":                       # a choice of order, 0..2
+            assert v in (0, 1, 2) and set(cands) <= {0, 1, 2}
+            continue
         assert v > 0 and all(c > 0 for c in cands)
-        if name in ("C_BATCH", "B_BATCH"):             # one candidate per lane of a warp
+        if name in ("C_BATCH", "B_BATCH", "T_BATCH"):  # one candidate per lane of a warp
             assert max(cands) <= 32 and v <= 32
 
 

@@ -74,6 +74,12 @@ def check_all(tec, off, col, thresholds):
     gt2, _ = g.edge_support()
     assert np.array_equal(_u32(gt2), t)
     g.set_core_staging(True)
+    # and so does the probe-row tiling, with any number of vertex-id ranges
+    for groups in (1, 3, 16, -1):
+        g.set_support_tiling(groups)
+        gt3, _ = g.edge_support()
+        assert np.array_equal(_u32(gt3), t), f"tiling with {groups} ranges"
+    g.set_support_tiling(0)
     g.free()
 
 
@@ -138,11 +144,13 @@ def test_complete_graph_chunked_rows(tec):
         col[u * (k - 1):(u + 1) * (k - 1)] = np.delete(ids, u)
     off = np.arange(0, k * (k - 1) + 1, k - 1, dtype=np.int64)
     g = _gpu_graph(tec, off, col, validate=False)
-    for core in (True, False):       # bitmap chunks of 8192 ids, hashed chunks of 4096
-        g.set_core_staging(core)
+    for core, groups in ((True, 0), (False, 0), (True, 2), (True, 7)):   # bitmap chunks of 8192 ids,
+        g.set_core_staging(core)                                         # hashed chunks of 4096, tiled
+        g.set_support_tiling(groups)
         t, w = g.edge_support()
         assert int(t.min()) == k - 2 and int(t.max()) == k - 2
         assert int(w.min()) == 0 and int(w.max()) == 0
+    g.set_support_tiling(0)
     lab, nc = g.full_pass(tec.TECTONIC, k - 2, 2 * (k - 1))       # exactly the common weight: keep all
     assert nc == 1 and int(lab.max()) == 0
     lab, nc = g.full_pass(tec.TECTONIC, k - 2 + 1, 2 * (k - 1))   # just above: drop all

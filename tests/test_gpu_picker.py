@@ -43,9 +43,25 @@ def test_forward_and_gradient_against_oracle(tec):
     assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go)
     big = np.abs(go) > 1e-3 * np.abs(go).max()
     np.testing.assert_allclose(g[big], go[big], rtol=1e-3)
-    # bf16 inference: close to float32
+    # bf16 inference: bf16 weights and activations, each input as two bf16
+    # terms; the output stays within a few bf16 roundings of float32
     yb = pk.forward(Xd, bf16=True).cpu().numpy()
-    assert np.max(np.abs(yb - y)) <= 0.05 * (np.abs(y).max() + 1)
+    assert np.max(np.abs(yb - y)) <= 2e-2 * (np.abs(y).max() + 1)
+    pk.free()
+
+
+def test_bf16_picks_the_float32_level_on_held_out_graphs(tec):
+    """The shipped picker's bfloat16 inference picks the same grid level as
+    its float32 inference on at least 99% of the 500 held-out DC-SBM graphs
+    (seeds 20000-20499, n in [1e3, 1e5])."""
+    from paper_2412_12382_gb300 import picker as P
+    held = P.build_dataset(list(range(20000, 20500)), 1000, 100000)
+    pk, _ = P.load(P.CHECKPOINT)
+    l32 = P.predict_levels(pk, held["feats"], bf16=False)
+    l16 = P.predict_levels(pk, held["feats"], bf16=True)
+    same = float((l32 == l16).float().mean().item())
+    print("bf16 same level on held-out graphs:", same)
+    assert same >= 0.99
     pk.free()
 
 

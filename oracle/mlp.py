@@ -4,8 +4,10 @@ Float64 numpy statement of the network the CUDA picker trains: 66 inputs ->
 128 (ReLU) -> 128 (ReLU) -> 1 output, loss = mean squared error, Adam
 (Kingma & Ba 2015) with bias correction.  The paper has no learned picker
 (it chooses thresholds by rules of thumb, Sec. IV-D); the architecture is the
-project's.  Parameter vector layout: W1 [128 x 66] row-major, b1 [128],
-W2 [128 x 128], b2 [128], w3 [128], b3 [1].
+project's.  A second objective, the soft-level ARI loss, mixes the squared
+error with the expected ARI lost by a Gaussian-smoothed level choice.
+Parameter vector layout: W1 [128 x 66] row-major, b1 [128], W2 [128 x 128],
+b2 [128], w3 [128], b3 [1].
 
 Parity unpinned by the paper: pinned by finite differences, closed forms and
 the Adam first-step identity (tests/test_oracle_mlp.py).
@@ -63,6 +65,45 @@ def loss_and_grad(theta, X, target):
     g["W1"] = dz1.T @ X
     g["b1"] = dz1.sum(0)
     return float(np.mean((y - target) ** 2)), pack(g)
+
+
+def soft_level_loss(y, L, sigma):
+    """Expected ARI loss of a smoothed level choice, per sample, and its
+    derivative in y.  The picker's level is round(64 y); here every grid
+    level i = 1..64 gets the weight w_i ~ exp(-(i - 64 y)^2 / (2 sigma^2))
+    (normalised to sum 1), and the loss is sum_i w_i L_i, L_i the ARI lost at
+    level i against the best level (L: N x 64).  As sigma -> 0 it tends to the
+    ARI lost at the nearest level.  d/dy = 64 / sigma^2 *
+    (sum_i w_i L_i (i - p) - loss * sum_i w_i (i - p)), p = 64 y."""
+    y = np.asarray(y, dtype=np.float64)
+    L = np.asarray(L, dtype=np.float64)
+    i = np.arange(1, L.shape[1] + 1, dtype=np.float64)
+    d = i[None, :] - 64.0 * y[:, None]
+    a = -d * d / (2.0 * sigma * sigma)
+    w = np.exp(a - a.max(axis=1, keepdims=True))
+    w /= w.sum(axis=1, keepdims=True)
+    val = (w * L).sum(axis=1)
+    dval = 64.0 / (sigma * sigma) * ((w * L * d).sum(axis=1) - val * (w * d).sum(axis=1))
+    return val, dval
+
+
+def mixed_loss_and_grad(theta, X, target, L, sigma, mix):
+    """mix * (mean squared error to target) + (1 - mix) * (mean soft-level
+    ARI loss), and its gradient by backpropagation."""
+    p = unpack(theta)
+    y, (X, z1, h1, z2, h2) = forward(theta, X)
+    n = X.shape[0]
+    t = np.asarray(target, dtype=np.float64)
+    sv, sd = soft_level_loss(y, L, sigma)
+    dy = (mix * 2.0 * (y - t) + (1.0 - mix) * sd) / n
+    g = {"w3": h2.T @ dy, "b3": np.array([dy.sum()])}
+    dz2 = np.outer(dy, p["w3"]) * (z2 > 0)
+    g["W2"] = dz2.T @ h1
+    g["b2"] = dz2.sum(0)
+    dz1 = (dz2 @ p["W2"]) * (z1 > 0)
+    g["W1"] = dz1.T @ X
+    g["b1"] = dz1.sum(0)
+    return float(np.mean(mix * (y - t) ** 2 + (1.0 - mix) * sv)), pack(g)
 
 
 def adam(theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -77,3 +77,42 @@ def test_training_reduces_loss():
         _, g = M.loss_and_grad(theta, X, t)
         theta, m, v = M.adam(theta, g, m, v, step)
     assert M.loss(theta, X, t) < 0.1 * l0
+
+
+def test_soft_level_loss_derivative_and_limits():
+    rng = np.random.default_rng(8)
+    L = rng.uniform(0, 0.3, (9, 64))
+    L[np.arange(9), rng.integers(0, 64, 9)] = 0.0
+    y = rng.uniform(0.05, 0.95, 9)
+    for sigma in (0.7, 1.5, 4.0):
+        v, dv = M.soft_level_loss(y, L, sigma)
+        h = 1e-6
+        vp, _ = M.soft_level_loss(y + h, L, sigma)
+        vm, _ = M.soft_level_loss(y - h, L, sigma)
+        np.testing.assert_allclose(dv, (vp - vm) / (2 * h), rtol=1e-5, atol=1e-7)
+        assert (v >= L.min(axis=1) - 1e-12).all() and (v <= L.max(axis=1) + 1e-12).all()
+    # a narrow window sits on the nearest level: the ARI lost there
+    v, _ = M.soft_level_loss(np.array([10 / 64, 33.2 / 64]), L[:2], 0.05)
+    np.testing.assert_allclose(v, [L[0, 9], L[1, 32]], rtol=1e-9, atol=1e-12)
+    # a flat table has no slope
+    _, dv = M.soft_level_loss(y, np.full((9, 64), 0.1), 1.0)
+    np.testing.assert_allclose(dv, 0.0, atol=1e-9)
+
+
+def test_mixed_loss_gradient_matches_central_differences():
+    X, t = _data(13, seed=4)
+    L = np.random.default_rng(5).uniform(0, 0.2, (13, 64))
+    theta = M.init(6)
+    theta[-1] = 0.4
+    for mix in (0.0, 0.3, 1.0):
+        lo, g = M.mixed_loss_and_grad(theta, X, t, L, 1.5, mix)
+        if mix == 1.0:
+            lm, gm = M.loss_and_grad(theta, X, t)
+            assert abs(lo - lm) < 1e-12 and np.allclose(g, gm)
+        rng = np.random.default_rng(int(mix * 10))
+        for k in rng.choice(M.NPARAM, 12, replace=False):
+            e = np.zeros(M.NPARAM)
+            e[k] = 1e-6
+            fp, _ = M.mixed_loss_and_grad(theta + e, X, t, L, 1.5, mix)
+            fm, _ = M.mixed_loss_and_grad(theta - e, X, t, L, 1.5, mix)
+            assert abs((fp - fm) / 2e-6 - g[k]) <= 1e-6 + 1e-4 * abs(g[k])

@@ -47,9 +47,13 @@ WORKLOADS = {
 # DRAM bytes per launch of the triangle-count stage from an ncu capture, per
 # unit of algorithmic bytes, valid only for the support.cu it was taken on
 # (see profiles/).  None until a capture exists for the current source.
-TRAFFIC_CAPTURE = {"support_sha": "cbc4243a25e3c702", "dram_per_alg_byte": 86.630 / 49.162954,
+TRAFFIC_CAPTURE = {"support_sha": "9f53b7b10502a1dc", "dram_per_alg_byte": 86.613 / 49.162954,
                    "source": "ncu DRAM bytes of the triangle-count stage's kernels at R-MAT scale 22, "
-                             "scaled by algorithmic bytes"}
+                             "scaled by algorithmic bytes",
+                   # the same counters taken directly on the R-MAT scale-26 launch (one-pass capture)
+                   "rmat26_bytes": 10731397195520 + 3483785178112 + 177139897856 + 3276615168,
+                   "rmat26_source": "ncu DRAM bytes (read + write) of k_support_core and k_support, one launch "
+                                    "each, on the R-MAT scale-26 workload itself"}
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -332,6 +336,12 @@ def bench_picker(reps=3):
     msf_ms, (best, best_ari) = _timed(sweep_msf, stream, reps + 1)
     got = g.ari(plab[None, :], truth, seg)[0]
     ari_all = g.ari(lab_all, truth, seg)
+    # the same picker with float32 inference, for the bf16 / fp32 comparison
+    p32, _ = g.pick_threshold(pk, seg, bf16=False)
+    p16, _ = g.pick_threshold(pk, seg, bf16=True)
+    cols32 = torch.arange(nseg, device="cuda")
+    got32 = ari_all[(p32 - 1).long(), cols32]
+    same_level = float((p32 == p16).float().mean().item())
     fixed_level = int(meta.get("eval", {}).get("fixed_level", 8)) - 1
     # the paper's rules of thumb (Sec. IV-D) on the same sweep, as baselines
     stats = g.sweep_stats(TECTONIC, PK.GRID_P, PK.GRID_Q, lab_all, seg)
@@ -350,6 +360,7 @@ def bench_picker(reps=3):
            "ratio_msf_including_support": (msf_ms + sup_ms) / (picker_ms + sup_ms),
            "same_best_both_sweeps": bool(torch.equal(best, best_i)),
            "mean_dARI": float(d.mean()), "p95_dARI": float(np.percentile(d, 95)), "max_dARI": float(d.max()),
+           "mean_dARI_fp32": float((best_ari - got32).mean().item()), "bf16_same_level_fraction": same_level,
            "mean_ARI_picker": float(got.mean()), "mean_ARI_best": float(best_ari.mean()),
            "mean_ARI_fixed": float(ari_all[fixed_level].mean()), "fixed_threshold": f"{fixed_level + 1}/128",
            "mean_ARI_R1_largest_jump": rule_ari["R1"], "mean_ARI_R2_modularity": rule_ari["R2"],
@@ -520,8 +531,13 @@ def main():
     sup_ms = statistics.mean(stage_ms[1])
     achieved = B_sup / (sup_ms / 1e3) / 1e9
     traffic = None
-    if TRAFFIC_CAPTURE["support_sha"] == support_sha() and TRAFFIC_CAPTURE["dram_per_alg_byte"]:
-        traffic = TRAFFIC_CAPTURE["dram_per_alg_byte"] * B_sup
+    traffic_source = None
+    if TRAFFIC_CAPTURE["support_sha"] == support_sha():
+        if args.workload == "rmat26" and TRAFFIC_CAPTURE["rmat26_bytes"]:
+            traffic, traffic_source = TRAFFIC_CAPTURE["rmat26_bytes"], TRAFFIC_CAPTURE["rmat26_source"]
+        elif TRAFFIC_CAPTURE["dram_per_alg_byte"]:
+            traffic = TRAFFIC_CAPTURE["dram_per_alg_byte"] * B_sup
+            traffic_source = TRAFFIC_CAPTURE["source"]
     pass_gbs = ab["B_alg_min"] / (ms_per_step / 1e3) / 1e9
 
     e2e = None
@@ -590,7 +606,9 @@ def main():
                                             "over the pass time, of the peak",
                          "kernel": "triangle-count stage (support kernels)",
                          "alg_bytes_per_launch": B_sup, "peak_kind": peak_kind,
-                         "traffic_source": TRAFFIC_CAPTURE["source"] if traffic else None},
+                         "traffic_source": traffic_source,
+                         "traffic_GBps": traffic / (sup_ms / 1e3) / 1e9 if traffic else None,
+                         "traffic_frac": traffic / (sup_ms / 1e3) / 1e9 / peak if traffic else None},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "gpu_launches_per_step": launches / args.steps, "clocks": clocks,
             "batched_sweep": sweep, "picker_vs_sweep": picker,

@@ -418,6 +418,24 @@ tec_status tec_picker_adam_step(tec_picker *p, const float *grad, float lr, floa
 tec_status tec_picker_train(tec_picker *p, const float *feats, const float *target, int64_t N, int epochs, int batch,
                             float lr, uint64_t seed, float *loss_out);
 
+/* The soft-level objective, for training the picker on what it is judged by.
+ * ari_loss (device, N x 64 float32): row s holds, for every grid level
+ * i = 1..64, the ARI that graph s loses at threshold i/128 against its best
+ * level.  Per sample the loss is mix * (y - target)^2 + (1 - mix) *
+ * sum_i w_i ari_loss[s][i], with w_i proportional to
+ * exp(-(i - 64 y)^2 / (2 sigma^2)) and summing to 1: the expected ARI lost
+ * by a level choice smoothed around 64 y (sigma in grid levels, 0.05..64;
+ * mix in [0, 1]; mix = 1 is tec_picker_loss_grad's squared error).
+ * tec_picker_soft_loss_grad: the mean loss (HOST, may be NULL; waits) and its
+ * gradient (device, may be NULL) like tec_picker_loss_grad.
+ * tec_picker_train_soft: tec_picker_train with this loss.  Not from the
+ * paper: the picker replaces the rules of thumb of Sec. IV-D. */
+tec_status tec_picker_soft_loss_grad(tec_picker *p, const float *feats, const float *target, const float *ari_loss,
+                                     int64_t N, float sigma, float mix, float *loss_out, float *grad_out);
+tec_status tec_picker_train_soft(tec_picker *p, const float *feats, const float *target, const float *ari_loss,
+                                 int64_t N, int epochs, int batch, float lr, uint64_t seed, float sigma, float mix,
+                                 float *loss_out);
+
 /* The learned threshold of every graph of a batch (the whole graph if
  * seg_off is NULL): tec_features, the picker network (bf16 != 0: bfloat16
  * inference as in tec_picker_forward) and the grid threshold of

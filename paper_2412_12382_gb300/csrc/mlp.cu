@@ -77,6 +77,9 @@ __global__ void __launch_bounds__(HID) k_forward(const float *__restrict__ P, co
     }
 }
 
+// With GIVEN, DY already holds dloss/dy of every sample (the soft-level
+// loss); otherwise dy is the squared error's 2 (y - t) / B.
+template <bool GIVEN>
 __global__ void __launch_bounds__(HID) k_backward(const float *__restrict__ P, const float *__restrict__ Z1,
                                                   const float *__restrict__ Z2, const float *__restrict__ Y,
                                                   const float *__restrict__ T, int64_t B, float *__restrict__ DY,
@@ -85,8 +88,8 @@ __global__ void __launch_bounds__(HID) k_backward(const float *__restrict__ P, c
     const int64_t b = blockIdx.x;
     if (b >= B) return;
     const int j = threadIdx.x;
-    const float dy = 2.f * (Y[b] - T[b]) / (float)B;
-    if (j == 0) DY[b] = dy;
+    const float dy = GIVEN ? DY[b] : 2.f * (Y[b] - T[b]) / (float)B;
+    if (!GIVEN && j == 0) DY[b] = dy;
     const float d2 = Z2[b * HID + j] > 0.f ? dy * P[OFF_W3 + j] : 0.f;
     DZ2[b * HID + j] = d2;
     sd[j] = d2;
@@ -132,6 +135,65 @@ __global__ void k_loss(const float *__restrict__ Y, const float *__restrict__ T,
         const double d = (double)Y[b] - (double)T[b];
         a += d * d;
     }
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = (float)(s[0] / (double)(B > 0 ? B : 1));
+}
+
+// Mixed objective per sample, one warp each: mix * (y - t)^2 + (1 - mix) *
+// sum_i w_i L_i, with w_i ~ exp(-(i - 64 y)^2 / (2 sigma^2)) over the grid
+// levels i = 1..64 (normalised) and L_i the ARI lost at level i.  Writes
+// dloss/dy / B to DY and the sample's loss to SL.
+__global__ void k_soft_dy(const float *__restrict__ Y, const float *__restrict__ T, const float *__restrict__ A,
+                          int64_t B, float sigma, float mix, float *__restrict__ DY, float *__restrict__ SL) {
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= B) return;
+    const int lane = (int)lane_id();
+    const float p = 64.f * Y[b];
+    const float inv = 1.f / (sigma * sigma);
+    float d[2], a[2], L[2];
+    for (int h = 0; h < 2; ++h) {
+        const int i = 1 + lane + 32 * h;
+        d[h] = (float)i - p;
+        a[h] = -0.5f * d[h] * d[h] * inv;
+        L[h] = A[b * 64 + i - 1];
+    }
+    float amax = fmaxf(a[0], a[1]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    float z = 0.f, wl = 0.f, wld = 0.f, wd = 0.f;
+    for (int h = 0; h < 2; ++h) {
+        const float w = expf(a[h] - amax);
+        z += w;
+        wl += w * L[h];
+        wld += w * L[h] * d[h];
+        wd += w * d[h];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        z += __shfl_xor_sync(0xffffffffu, z, o);
+        wl += __shfl_xor_sync(0xffffffffu, wl, o);
+        wld += __shfl_xor_sync(0xffffffffu, wld, o);
+        wd += __shfl_xor_sync(0xffffffffu, wd, o);
+    }
+    if (lane == 0) {
+        const float val = wl / z;
+        const float dval = 64.f * inv * (wld / z - val * (wd / z));
+        const float e = Y[b] - T[b];
+        DY[b] = (mix * 2.f * e + (1.f - mix) * dval) / (float)B;
+        SL[b] = mix * e * e + (1.f - mix) * val;
+    }
+}
+
+// Mean of the per-sample losses SL (one block).
+__global__ void k_mean(const float *__restrict__ SL, int64_t B, float *out) {
+    __shared__ double s[256];
+    double a = 0.0;
+    for (int64_t b = threadIdx.x; b < B; b += blockDim.x) a += (double)SL[b];
     s[threadIdx.x] = a;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -187,6 +249,15 @@ __global__ void k_gather(const float *__restrict__ F, const float *__restrict__ 
     if (threadIdx.x == 0) TB[b] = T[src];
 }
 
+// The ARI-loss rows (64 each) of the same samples as k_gather.
+__global__ void k_gather_rows(const float *__restrict__ L, int64_t N, int64_t first, int64_t B, int bits,
+                              uint64_t key, float *__restrict__ AB) {
+    const int64_t b = blockIdx.x;
+    if (b >= B) return;
+    const int64_t src = key ? shuffle_index(first + b, N, bits, key) : first + b;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) AB[b * 64 + i] = L[src * 64 + i];
+}
+
 // Grid threshold per graph: b = clamp(round(64 y), 1, 64), theta = b / 128.
 __global__ void k_pick(const float *y, int64_t N, int64_t *p, int64_t *q) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -219,16 +290,17 @@ struct tec_picker {
     int64_t cap = 0;                     // batch capacity of the work buffers
     float *X = nullptr, *T = nullptr, *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr;
     float *DY = nullptr, *DZ1 = nullptr, *DZ2 = nullptr, *loss = nullptr;
+    float *A = nullptr, *SL = nullptr;   // soft-level loss: ARI-loss rows (64 per sample), per-sample losses
     int64_t step = 0;
 };
 
 namespace {
 
 void picker_free_work(tec_picker *p) {
-    float *bufs[] = {p->X, p->T, p->Z1, p->Z2, p->Y, p->DY, p->DZ1, p->DZ2};
+    float *bufs[] = {p->X, p->T, p->Z1, p->Z2, p->Y, p->DY, p->DZ1, p->DZ2, p->A, p->SL};
     for (float *b : bufs)
         if (b) cudaFree(b);
-    p->X = p->T = p->Z1 = p->Z2 = p->Y = p->DY = p->DZ1 = p->DZ2 = nullptr;
+    p->X = p->T = p->Z1 = p->Z2 = p->Y = p->DY = p->DZ1 = p->DZ2 = p->A = p->SL = nullptr;
     p->cap = 0;
 }
 
@@ -236,9 +308,9 @@ tec_status picker_work(tec_picker *p, int64_t B) {
     if (p->cap >= B) return TEC_OK;
     picker_free_work(p);
     const int64_t c = B < 256 ? 256 : B;
-    float **bufs[] = {&p->X, &p->T, &p->Z1, &p->Z2, &p->Y, &p->DY, &p->DZ1, &p->DZ2};
-    const int64_t sizes[] = {c * IN, c, c * HID, c * HID, c, c, c * HID, c * HID};
-    for (int i = 0; i < 8; ++i) {
+    float **bufs[] = {&p->X, &p->T, &p->Z1, &p->Z2, &p->Y, &p->DY, &p->DZ1, &p->DZ2, &p->A, &p->SL};
+    const int64_t sizes[] = {c * IN, c, c * HID, c * HID, c, c, c * HID, c * HID, c * 64, c};
+    for (int i = 0; i < 10; ++i) {
         cudaError_t e = cudaMalloc((void **)bufs[i], (size_t)sizes[i] * sizeof(float));
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -250,14 +322,21 @@ tec_status picker_work(tec_picker *p, int64_t B) {
     return TEC_OK;
 }
 
-// Forward + backward + gradient of one batch already in p->X / p->T.
-tec_status picker_batch_grad(tec_picker *p, int64_t B) {
+// Forward + backward + gradient of one batch already in p->X / p->T (and,
+// for the soft-level loss (soft), p->A).
+tec_status picker_batch_grad(tec_picker *p, int64_t B, bool soft = false, float sigma = 1.f, float mix = 1.f) {
     cudaStream_t s = p->stream;
     k_forward<false><<<(unsigned)B, HID, 0, s>>>(p->P, p->X, B, p->Z1, p->Z2, p->Y);
-    k_backward<<<(unsigned)B, HID, 0, s>>>(p->P, p->Z1, p->Z2, p->Y, p->T, B, p->DY, p->DZ1, p->DZ2);
+    if (soft) {
+        k_soft_dy<<<(unsigned)ceil_div(B * 32, 256), 256, 0, s>>>(p->Y, p->T, p->A, B, sigma, mix, p->DY, p->SL);
+        k_backward<true><<<(unsigned)B, HID, 0, s>>>(p->P, p->Z1, p->Z2, p->Y, p->T, B, p->DY, p->DZ1, p->DZ2);
+    } else {
+        k_backward<false><<<(unsigned)B, HID, 0, s>>>(p->P, p->Z1, p->Z2, p->Y, p->T, B, p->DY, p->DZ1, p->DZ2);
+    }
     k_grad<<<(unsigned)ceil_div(NPARAM, 256), 256, 0, s>>>(p->X, p->Z1, p->Z2, p->DY, p->DZ1, p->DZ2, B, p->G);
-    k_loss<<<1, 256, 0, s>>>(p->Y, p->T, B, p->loss);
-    count_launches(4);
+    if (soft) k_mean<<<1, 256, 0, s>>>(p->SL, B, p->loss);
+    else k_loss<<<1, 256, 0, s>>>(p->Y, p->T, B, p->loss);
+    count_launches(soft ? 5 : 4);
     TEC_CUDA(cudaGetLastError());
     return TEC_OK;
 }
@@ -411,10 +490,9 @@ tec_status tec_picker_adam_step(tec_picker *p, const float *grad, float lr, floa
     return picker_adam(p, lr, beta1, beta2, eps);
 }
 
-tec_status tec_picker_train(tec_picker *p, const float *feats, const float *target, int64_t N, int epochs, int batch,
-                            float lr, uint64_t seed, float *loss_out) {
-    clear_error();
-    if (!p || N <= 0 || !feats || !target || epochs < 0 || batch < 1) return set_error(TEC_EINVAL, "bad argument");
+static tec_status train_impl(tec_picker *p, const float *feats, const float *target, const float *ari_loss,
+                             int64_t N, int epochs, int batch, float lr, uint64_t seed, bool soft, float sigma,
+                             float mix, float *loss_out) {
     TEC_TRY(picker_work(p, batch));
     int bits = 1;
     while (((int64_t)1 << bits) < N) ++bits;
@@ -426,8 +504,9 @@ tec_status tec_picker_train(tec_picker *p, const float *feats, const float *targ
         for (int64_t first = 0; first < N; first += batch) {
             const int64_t B = N - first < batch ? N - first : batch;
             k_gather<<<(unsigned)B, 128, 0, p->stream>>>(feats, target, N, first, B, bits, key, p->X, p->T);
-            count_launches(1);
-            TEC_TRY(picker_batch_grad(p, B));
+            if (soft) k_gather_rows<<<(unsigned)B, 64, 0, p->stream>>>(ari_loss, N, first, B, bits, key, p->A);
+            count_launches(soft ? 2 : 1);
+            TEC_TRY(picker_batch_grad(p, B, soft, sigma, mix));
             TEC_TRY(picker_adam(p, lr, 0.9f, 0.999f, 1e-8f));
             if (loss_out) {
                 float l = 0.f;
@@ -442,6 +521,49 @@ tec_status tec_picker_train(tec_picker *p, const float *feats, const float *targ
         for (int e = 0; e < epochs; ++e) loss_out[e] = ep_loss[e];
     TEC_CUDA(cudaStreamSynchronize(p->stream));
     return TEC_OK;
+}
+
+tec_status tec_picker_train(tec_picker *p, const float *feats, const float *target, int64_t N, int epochs, int batch,
+                            float lr, uint64_t seed, float *loss_out) {
+    clear_error();
+    if (!p || N <= 0 || !feats || !target || epochs < 0 || batch < 1) return set_error(TEC_EINVAL, "bad argument");
+    return train_impl(p, feats, target, nullptr, N, epochs, batch, lr, seed, false, 1.f, 1.f, loss_out);
+}
+
+static tec_status check_soft(float sigma, float mix) {
+    if (!(sigma >= 0.05f && sigma <= 64.f)) return set_error(TEC_EINVAL, "sigma must lie in [0.05, 64]");
+    if (!(mix >= 0.f && mix <= 1.f)) return set_error(TEC_EINVAL, "mix must lie in [0, 1]");
+    return TEC_OK;
+}
+
+tec_status tec_picker_soft_loss_grad(tec_picker *p, const float *feats, const float *target, const float *ari_loss,
+                                     int64_t N, float sigma, float mix, float *loss_out, float *grad_out) {
+    clear_error();
+    if (!p || N <= 0 || !feats || !target || !ari_loss) return set_error(TEC_EINVAL, "bad argument");
+    if (N > 2147483647) return set_error(TEC_EINVAL, "too many samples");
+    TEC_TRY(check_soft(sigma, mix));
+    TEC_TRY(picker_work(p, N));
+    TEC_CUDA(cudaMemcpyAsync(p->X, feats, (size_t)N * IN * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
+    TEC_CUDA(cudaMemcpyAsync(p->T, target, (size_t)N * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
+    TEC_CUDA(cudaMemcpyAsync(p->A, ari_loss, (size_t)N * 64 * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
+    TEC_TRY(picker_batch_grad(p, N, true, sigma, mix));
+    if (grad_out)
+        TEC_CUDA(cudaMemcpyAsync(grad_out, p->G, NPARAM * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
+    if (loss_out) {
+        TEC_CUDA(cudaMemcpyAsync(loss_out, p->loss, sizeof(float), cudaMemcpyDeviceToHost, p->stream));
+        TEC_CUDA(cudaStreamSynchronize(p->stream));
+    }
+    return TEC_OK;
+}
+
+tec_status tec_picker_train_soft(tec_picker *p, const float *feats, const float *target, const float *ari_loss,
+                                 int64_t N, int epochs, int batch, float lr, uint64_t seed, float sigma, float mix,
+                                 float *loss_out) {
+    clear_error();
+    if (!p || N <= 0 || !feats || !target || !ari_loss || epochs < 0 || batch < 1)
+        return set_error(TEC_EINVAL, "bad argument");
+    TEC_TRY(check_soft(sigma, mix));
+    return train_impl(p, feats, target, ari_loss, N, epochs, batch, lr, seed, true, sigma, mix, loss_out);
 }
 
 }  // extern "C"

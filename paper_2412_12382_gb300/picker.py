@@ -119,6 +119,12 @@ def init_params(seed: int = 0):
     return np.concatenate(parts).astype(np.float32)
 
 
+def ari_loss_rows(dataset):
+    """N x 64 float32: the ARI each graph loses at each grid level against its
+    best level (the table the soft-level loss weighs)."""
+    return (dataset["best_ari"][None, :] - dataset["ari"]).T.contiguous().float()
+
+
 def train(dataset, epochs=300, batch=256, lr=1e-3, seed=0):
     picker = T.Picker(init_params(seed))
     losses = picker.train(dataset["feats"], dataset["target"], epochs, batch, lr, seed)

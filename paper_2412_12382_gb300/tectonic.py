@@ -79,6 +79,9 @@ SIGNATURES = {
     "tec_picker_adam_step": ([_P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float], ctypes.c_int),
     "tec_picker_train": ([_P, _P, _P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64, _P],
                          ctypes.c_int),
+    "tec_picker_soft_loss_grad": ([_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, _P, _P], ctypes.c_int),
+    "tec_picker_train_soft": ([_P, _P, _P, _P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64,
+                               ctypes.c_float, ctypes.c_float, _P], ctypes.c_int),
     "tec_picker_thresholds": ([_P, _I64, _P, _P, _P], ctypes.c_int),
     "tec_pick_threshold": ([_P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P], ctypes.c_int),
     "tec_sweep_stats": ([_P, ctypes.c_int, _P, _P, ctypes.c_int, _P, _P, ctypes.c_int, _P], ctypes.c_int),
@@ -560,6 +563,25 @@ class Picker:
 
     def adam_step(self, grad=None, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
         check(self._lib.tec_picker_adam_step(self._h, _ptr(grad), lr, beta1, beta2, eps))
+
+    def soft_loss_grad(self, feats, target, ari_loss, sigma: float, mix: float):
+        """Soft-level loss (mean) and its gradient (tec_picker_soft_loss_grad)."""
+        torch = _torch()
+        g = torch.empty(PICKER_PARAMS, dtype=torch.float32, device="cuda")
+        loss = ctypes.c_float(0.0)
+        check(self._lib.tec_picker_soft_loss_grad(self._h, _ptr(feats.contiguous()), _ptr(target.contiguous()),
+                                                  _ptr(ari_loss.contiguous()), feats.shape[0], float(sigma),
+                                                  float(mix), ctypes.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def train_soft(self, feats, target, ari_loss, epochs: int, batch: int = 256, lr: float = 1e-3, seed: int = 0,
+                   sigma: float = 1.5, mix: float = 0.5):
+        """tec_picker_train with the soft-level loss; returns the mean loss per epoch."""
+        losses = np.empty(max(epochs, 1), dtype=np.float32)
+        check(self._lib.tec_picker_train_soft(self._h, _ptr(feats.contiguous()), _ptr(target.contiguous()),
+                                              _ptr(ari_loss.contiguous()), feats.shape[0], int(epochs), int(batch),
+                                              float(lr), int(seed), float(sigma), float(mix), _ptr(losses)))
+        return losses[:epochs]
 
     def train(self, feats, target, epochs: int, batch: int = 256, lr: float = 1e-3, seed: int = 0):
         losses = np.empty(max(epochs, 1), dtype=np.float32)

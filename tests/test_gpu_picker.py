@@ -65,6 +65,28 @@ def test_bf16_picks_the_float32_level_on_held_out_graphs(tec):
     pk.free()
 
 
+def test_soft_level_loss_and_gradient_against_oracle(tec):
+    import torch
+    from paper_2412_12382_gb300.tectonic import Picker
+    X, t = _data(150, 9)
+    L = np.random.default_rng(10).uniform(0, 0.3, (150, 64)).astype(np.float32)
+    theta = M.init(11).astype(np.float32)
+    theta[-1 - 128:-1] *= 0.02           # small w3: outputs near b3, levels inside the grid
+    theta[-1] = 0.35
+    pk = Picker(theta)
+    y0, _ = M.forward(theta.astype(np.float64), X.astype(np.float64))
+    assert ((64 * y0 > 3) & (64 * y0 < 62)).mean() > 0.9
+    Xd, td, Ld = (torch.from_numpy(a).cuda() for a in (X, t, L))
+    for sigma, mix in ((1.5, 0.3), (0.8, 0.0), (3.0, 1.0)):
+        loss, g = pk.soft_loss_grad(Xd, td, Ld, sigma, mix)
+        lo, go = M.mixed_loss_and_grad(theta.astype(np.float64), X.astype(np.float64), t.astype(np.float64),
+                                       L.astype(np.float64), sigma, mix)
+        g = g.cpu().numpy()
+        assert abs(loss - lo) <= 1e-4 * abs(lo) + 1e-7
+        assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go)
+    pk.free()
+
+
 def test_adam_step_against_oracle(tec):
     import torch
     from paper_2412_12382_gb300.tectonic import Picker

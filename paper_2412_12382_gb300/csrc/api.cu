@@ -202,7 +202,7 @@ bool ensure_tiling(tec_graph *g, int groups) {
 }
 
 void free_graph_memory(tec_graph *g) {
-    void *ptrs[] = {g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->parent, g->tasks, g->sym_rows, g->or_rows,
+    void *ptrs[] = {g->off, g->col, g->deg, g->ooff, g->ocol, g->t, g->keep, g->parent, g->tasks, g->sym_rows, g->or_rows, g->osrc,
                     g->flags, g->tile_cnt, g->tile_base, g->bsum, g->uoff, g->ucnt, g->labels, g->lvl, g->best,
                     g->fu, g->fv, g->bucket, g->thr, g->sw_ncomp, g->seg_hist, g->ari_sums,
                     g->ari_size, g->ari_keys, g->ari_cnt, g->msf_u, g->msf_v, g->msf_k, g->msf_cnt, g->msf_changed,
@@ -245,7 +245,7 @@ tec_status reset_counter(tec_graph *g, int which) {
 tec_status ensure_oriented(tec_graph *g) {
     if (g->oriented) return TEC_OK;
     TEC_CUDA(launch_orient(g->off, g->col, g->deg, g->n, g->nnz, g->sym_rows, g->flags, g->tile_cnt, g->tile_base,
-                           g->bsum, g->ooff, g->ocol, g->m, g->ctr, g->stream));
+                           g->bsum, g->ooff, g->ocol, g->osrc, g->m, g->ctr, g->stream));
     TEC_CUDA(launch_tile_rows(g->ooff, g->n, g->m, g->or_rows, g->stream));
     g->oriented = true;
     g->supported = g->pruned = g->hooked = false;
@@ -378,7 +378,7 @@ tec_status run_full_pass(tec_graph *g, int measure, int64_t p, int64_t q, int32_
     TEC_TRY(reset_counter(g, C_NCOMP));
     TEC_CUDA(launch_cc_init(g->parent, g->n, g->stream));
     PruneArgs a{cmp, p, q, true};
-    TEC_CUDA(launch_prune(g->ooff, g->ocol, g->deg, cts, g->n, g->m, g->or_rows, a, g->keep, g->parent, g->ctr, g->stream));
+    TEC_CUDA(launch_prune(g->ooff, g->ocol, g->deg, cts, g->n, g->m, g->or_rows, g->osrc, a, g->keep, g->parent, g->ctr, g->stream));
     g->pruned = g->hooked = true;
     g->last_measure = measure;
     g->last_p = p;
@@ -459,7 +459,7 @@ tec_status tec_features(tec_graph *g, const int64_t *seg_off, int nseg, float *f
     const int ns = seg_off ? nseg : 1;
     TEC_TRY(ensure_seg_scratch(g, ns));
     TEC_TRY(ensure_support(g));
-    TEC_CUDA(launch_features(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, g->or_rows, seg_off, nseg, g->seg_hist, feat_out, g->ctr,
+    TEC_CUDA(launch_features(g->ooff, g->ocol, g->deg, g->t, g->n, g->m, g->or_rows, g->osrc, seg_off, nseg, g->seg_hist, feat_out, g->ctr,
                              g->stream));
     return TEC_OK;
 }
@@ -565,6 +565,7 @@ tec_status tec_graph_create(int64_t n_cap, int64_t nnz_cap, void *stream, tec_gr
     if (s == TEC_OK) s = dalloc(&g->flags, ntiles * (TILE / 32), "orientation bits");
     if (s == TEC_OK) s = dalloc(&g->sym_rows, tile_rows_size(nnz_cap), "tile rows");
     if (s == TEC_OK) s = dalloc(&g->or_rows, tile_rows_size(g->m_cap), "tile rows");
+    if (s == TEC_OK) s = dalloc(&g->osrc, g->m_cap, "edge sources");
     if (s == TEC_OK) s = dalloc(&g->tile_cnt, ntiles + 1, "tile counts");
     if (s == TEC_OK) s = dalloc(&g->tile_base, ntiles + 1, "tile offsets");
     if (s == TEC_OK) s = dalloc(&g->bsum, scan_bsum_size(scan_len), "scan partials");
@@ -777,7 +778,7 @@ tec_status tec_prune(tec_graph *g, tec_measure measure, int64_t p, int64_t q, ui
     TEC_TRY(measure_counts(g, (int)measure, &cts, &cmp));
     TEC_TRY(reset_counter(g, C_KEPT));
     PruneArgs a{cmp, p, q, false};
-    TEC_CUDA(launch_prune(g->ooff, g->ocol, g->deg, cts, g->n, g->m, g->or_rows, a, g->keep, g->parent, g->ctr, g->stream));
+    TEC_CUDA(launch_prune(g->ooff, g->ocol, g->deg, cts, g->n, g->m, g->or_rows, g->osrc, a, g->keep, g->parent, g->ctr, g->stream));
     g->pruned = true;
     g->hooked = false;
     g->last_measure = (int)measure;
@@ -805,7 +806,7 @@ tec_status tec_components(tec_graph *g, int32_t *labels_out, int64_t *ncomp_out)
     TEC_TRY(debug_refresh_caps(g));
     if (!g->hooked) {
         TEC_CUDA(launch_cc_init(g->parent, g->n, g->stream));
-        TEC_CUDA(launch_cc_hook(g->ooff, g->ocol, g->keep, g->n, g->m, g->or_rows, g->parent, g->ctr, g->stream));
+        TEC_CUDA(launch_cc_hook(g->ooff, g->ocol, g->keep, g->n, g->m, g->or_rows, g->osrc, g->parent, g->ctr, g->stream));
         g->hooked = true;
     }
     TEC_TRY(reset_counter(g, C_NCOMP));
@@ -1035,7 +1036,7 @@ tec_status tec_prune_components_batch(tec_graph *g, tec_measure measure, const i
     TEC_TRY(measure_counts(g, (int)measure, &cts, &cmp));
     TEC_TRY(reset_counter(g, C_KEPT));
     TEC_CUDA(launch_cc_init(g->parent, g->n, g->stream));
-    TEC_CUDA(launch_prune_seg(g->ooff, g->ocol, g->deg, cts, g->n, g->m, g->or_rows, cmp, p, q, seg_off, nseg, true,
+    TEC_CUDA(launch_prune_seg(g->ooff, g->ocol, g->deg, cts, g->n, g->m, g->or_rows, g->osrc, cmp, p, q, seg_off, nseg, true,
                               g->keep, g->parent, g->ctr, g->stream));
     g->pruned = g->hooked = true;
     TEC_CUDA(cudaMemsetAsync(g->sw_ncomp, 0, (size_t)nseg * sizeof(unsigned long long), g->stream));

@@ -18,7 +18,7 @@ __global__ void k_cc_init(int32_t *parent, int64_t n) {
 // every edge whose keep bit is set.
 __global__ void __launch_bounds__(TILE_THREADS)
 k_cc_hook(const int64_t *ooff, const int32_t *ocol, const uint32_t *keep, int64_t n, int64_t m,
-          const int32_t *orows, int32_t *parent, unsigned long long *ctr) {
+          const int32_t *orows, const int32_t *osrc, int32_t *parent, unsigned long long *ctr) {
     if (graph_bad(ctr)) return;
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
     int64_t r0, r1;
@@ -27,7 +27,7 @@ k_cc_hook(const int64_t *ooff, const int32_t *ocol, const uint32_t *keep, int64_
         const int64_t j = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
         if (j >= m) break;
         if (!((keep[j >> 5] >> (j & 31)) & 1u)) continue;
-        const int64_t u = row_search(ooff, r0, r1, j);
+        const int64_t u = edge_source(osrc, ooff, r0, r1, j);
         uf_link(parent, (int32_t)u, ocol[j], ctr);
     }
 }
@@ -62,9 +62,10 @@ cudaError_t launch_cc_init(int32_t *parent, int64_t n, cudaStream_t s) {
 }
 
 cudaError_t launch_cc_hook(const int64_t *ooff, const int32_t *ocol, const uint32_t *keep, int64_t n,
-                           int64_t m, const int32_t *orows, int32_t *parent, unsigned long long *ctr, cudaStream_t s) {
+                           int64_t m, const int32_t *orows, const int32_t *osrc, int32_t *parent,
+                           unsigned long long *ctr, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
-    k_cc_hook<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, keep, n, m, orows, parent, ctr);
+    k_cc_hook<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, keep, n, m, orows, osrc, parent, ctr);
     count_launches(1);
     return cudaGetLastError();
 }

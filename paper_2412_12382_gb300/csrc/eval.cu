@@ -44,7 +44,8 @@ __device__ __forceinline__ int seg_of(const int64_t *seg_off, int nseg, int64_t 
 
 __global__ void __launch_bounds__(TILE_THREADS)
 k_feat_hist(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t, int64_t n, int64_t m,
-            const int32_t *orows, const int64_t *seg_off, int nseg, unsigned int *hist, unsigned long long *ctr) {
+            const int32_t *orows, const int32_t *osrc, const int64_t *seg_off, int nseg, unsigned int *hist,
+            unsigned long long *ctr) {
     __shared__ unsigned int s_h[NBINS];
     if (graph_bad(ctr)) return;
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
@@ -60,7 +61,7 @@ k_feat_hist(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const 
         const bool valid = j < m;
         int64_t b = -1, u = 0;
         if (valid) {
-            u = row_search(ooff, r0, r1, j);
+            u = edge_source(osrc, ooff, r0, r1, j);
             const int64_t s = (int64_t)deg[u] + deg[ocol[j]];
             // b = floor(128 t / s): a float quotient (error far below 1)
             // corrected by exact integer comparisons
@@ -509,13 +510,13 @@ inline unsigned grid_for(int64_t work) {
 }  // namespace
 
 cudaError_t launch_features(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
-                            int64_t n, int64_t m, const int32_t *orows, const int64_t *seg_off, int nseg,
-                            unsigned int *hist, float *feat, unsigned long long *ctr, cudaStream_t s) {
+                            int64_t n, int64_t m, const int32_t *orows, const int32_t *osrc, const int64_t *seg_off,
+                            int nseg, unsigned int *hist, float *feat, unsigned long long *ctr, cudaStream_t s) {
     const int ns = seg_off ? nseg : 1;
     cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)ns * NBINS * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     if (m > 0)
-        k_feat_hist<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, seg_off, ns,
+        k_feat_hist<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, osrc, seg_off, ns,
                                                                          hist, ctr);
     k_feat_final<<<(unsigned)ceil_div((int64_t)ns * 32, 256), 256, 0, s>>>(hist, seg_off, ns, n, feat);
     count_launches(m > 0 ? 2 : 1);

@@ -112,7 +112,7 @@ k_orient_flags(const int64_t *off, const int32_t *col, const int32_t *deg, int64
 // ooff[u] for every row that starts (or, if empty, sits) at an entry of this tile.
 __global__ void __launch_bounds__(TILE_THREADS)
 k_orient_fill(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz, const int32_t *trow,
-              const uint32_t *flags, const int64_t *tile_base, int64_t *ooff, int32_t *ocol, int64_t m,
+              const uint32_t *flags, const int64_t *tile_base, int64_t *ooff, int32_t *ocol, int32_t *osrc, int64_t m,
               unsigned long long *ctr) {
     __shared__ int s_wc[TILE_THREADS / 32];
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
@@ -142,8 +142,12 @@ k_orient_fill(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz, co
                 for (int64_t x = u - 1; x >= 0 && off[x] == k; --x) ooff[x] = pos;
             }
             if ((word >> lane) & 1u) {
-                if (pos < m) ocol[pos] = col[k];
-                else flag_status(ctr, ST_BADGRAPH);
+                if (pos < m) {
+                    ocol[pos] = col[k];
+                    if (osrc) osrc[pos] = (int32_t)u;
+                } else {
+                    flag_status(ctr, ST_BADGRAPH);
+                }
             }
         }
         carry += total;
@@ -221,7 +225,7 @@ cudaError_t launch_validate_entries(const int64_t *off, const int32_t *col, int6
 
 cudaError_t launch_orient(const int64_t *off, const int32_t *col, const int32_t *deg, int64_t n,
                           int64_t nnz, const int32_t *trow, uint32_t *flags, int64_t *tile_cnt, int64_t *tile_base,
-                          int64_t *bsum, int64_t *ooff, int32_t *ocol, int64_t m,
+                          int64_t *bsum, int64_t *ooff, int32_t *ocol, int32_t *osrc, int64_t m,
                           unsigned long long *ctr, cudaStream_t s) {
     const int64_t ntiles = ceil_div(nnz, TILE);
     if (ntiles > 0) {
@@ -230,7 +234,7 @@ cudaError_t launch_orient(const int64_t *off, const int32_t *col, const int32_t 
         cudaError_t e = scan_exclusive_i64(tile_cnt, ntiles, tile_base, bsum, s);
         if (e != cudaSuccess) return e;
         k_orient_fill<<<(unsigned)ntiles, TILE_THREADS, 0, s>>>(off, col, n, nnz, trow, flags, tile_base, ooff,
-                                                               ocol, m, ctr);
+                                                               ocol, osrc, m, ctr);
         count_launches(1);
     } else {
         cudaError_t e = scan_exclusive_i64(tile_cnt, 0, tile_base, bsum, s);

@@ -22,8 +22,8 @@ namespace {
 template <bool HOOK, bool WIDE>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_prune(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t, int64_t n,
-        int64_t m, const int32_t *orows, int measure, int64_t p, int64_t q, uint32_t *keep, int32_t *parent,
-        unsigned long long *ctr) {
+        int64_t m, const int32_t *orows, const int32_t *osrc, int measure, int64_t p, int64_t q, uint32_t *keep,
+        int32_t *parent, unsigned long long *ctr) {
     __shared__ int ws[TILE_THREADS / 32];
     if (graph_bad(ctr)) return;
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
@@ -36,7 +36,7 @@ k_prune(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint
         const int64_t j = jw + lane;
         bool kp = false;
         if (j < m) {
-            const int64_t u = row_search(ooff, r0, r1, j);
+            const int64_t u = edge_source(osrc, ooff, r0, r1, j);
             const int32_t v = ocol[j];
             const int64_t s = (int64_t)deg[u] + deg[v];
             kp = keep_edge<WIDE>(measure, t[j], s, p, q);
@@ -60,8 +60,8 @@ k_prune(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint
 template <bool HOOK>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_prune_seg(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t, int64_t n, int64_t m,
-            const int32_t *orows, int measure, const int64_t *sp, const int64_t *sq, const int64_t *seg_off, int nseg,
-            uint32_t *keep, int32_t *parent, unsigned long long *ctr) {
+            const int32_t *orows, const int32_t *osrc, int measure, const int64_t *sp, const int64_t *sq,
+            const int64_t *seg_off, int nseg, uint32_t *keep, int32_t *parent, unsigned long long *ctr) {
     __shared__ int ws[TILE_THREADS / 32];
     if (graph_bad(ctr)) return;
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
@@ -89,7 +89,7 @@ k_prune_seg(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const 
         const int64_t j = jw + lane;
         bool kp = false;
         if (j < m) {
-            const int64_t u = row_search(ooff, r0, r1, j);
+            const int64_t u = edge_source(osrc, ooff, r0, r1, j);
             int lo = s0, hi = s1;                    // segment of u
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -181,31 +181,32 @@ k_export(const int64_t *off, const int32_t *col, const int32_t *deg, const int64
 }  // namespace
 
 cudaError_t launch_prune(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
-                         int64_t n, int64_t m, const int32_t *orows, PruneArgs a, uint32_t *keep, int32_t *parent,
+                         int64_t n, int64_t m, const int32_t *orows, const int32_t *osrc, PruneArgs a, uint32_t *keep,
+                         int32_t *parent,
                          unsigned long long *ctr, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)ceil_div(m, TILE);
     const bool wide = needs_wide(a.p, a.q);
     if (a.hook) {
-        if (wide) k_prune<true, true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, a.measure, a.p, a.q, keep, parent, ctr);
-        else k_prune<true, false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, a.measure, a.p, a.q, keep, parent, ctr);
+        if (wide) k_prune<true, true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, osrc, a.measure, a.p, a.q, keep, parent, ctr);
+        else k_prune<true, false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, osrc, a.measure, a.p, a.q, keep, parent, ctr);
     } else {
-        if (wide) k_prune<false, true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, a.measure, a.p, a.q, keep, parent, ctr);
-        else k_prune<false, false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, a.measure, a.p, a.q, keep, parent, ctr);
+        if (wide) k_prune<false, true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, osrc, a.measure, a.p, a.q, keep, parent, ctr);
+        else k_prune<false, false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, osrc, a.measure, a.p, a.q, keep, parent, ctr);
     }
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prune_seg(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
-                             int64_t n, int64_t m, const int32_t *orows, int measure, const int64_t *sp,
-                             const int64_t *sq,
+                             int64_t n, int64_t m, const int32_t *orows, const int32_t *osrc, int measure,
+                             const int64_t *sp, const int64_t *sq,
                              const int64_t *seg_off, int nseg, bool hook, uint32_t *keep, int32_t *parent,
                              unsigned long long *ctr, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)ceil_div(m, TILE);
-    if (hook) k_prune_seg<true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, measure, sp, sq, seg_off, nseg, keep, parent, ctr);
-    else k_prune_seg<false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, measure, sp, sq, seg_off, nseg, keep, parent, ctr);
+    if (hook) k_prune_seg<true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, osrc, measure, sp, sq, seg_off, nseg, keep, parent, ctr);
+    else k_prune_seg<false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, osrc, measure, sp, sq, seg_off, nseg, keep, parent, ctr);
     count_launches(1);
     return cudaGetLastError();
 }

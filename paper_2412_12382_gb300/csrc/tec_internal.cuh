@@ -99,9 +99,10 @@ cudaError_t launch_validate(const int64_t *off, const int32_t *col, int64_t n, i
                             unsigned long long *ctr, cudaStream_t s);
 cudaError_t launch_validate_entries(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz,
                                     const int32_t *trow, unsigned long long *ctr, cudaStream_t s);
+// osrc (m entries, or nullptr) receives the source row of every oriented edge.
 cudaError_t launch_orient(const int64_t *off, const int32_t *col, const int32_t *deg, int64_t n,
                           int64_t nnz, const int32_t *trow, uint32_t *flags, int64_t *tile_cnt, int64_t *tile_base,
-                          int64_t *bsum, int64_t *ooff, int32_t *ocol, int64_t m,
+                          int64_t *bsum, int64_t *ooff, int32_t *ocol, int32_t *osrc, int64_t m,
                           unsigned long long *ctr, cudaStream_t s);
 
 // support.cu: t[j] for every oriented edge (zeroed inside).  `flags` are the
@@ -165,12 +166,15 @@ struct PruneArgs {
     int64_t p, q;
     bool hook;          // also union the endpoints of every kept edge into `parent`
 };
-// orows: the tile-row table of the oriented CSR (or nullptr).
+// orows: the tile-row table of the oriented CSR, osrc its per-edge source
+// rows (either may be nullptr).
 cudaError_t launch_prune(const int64_t *ooff, const int32_t *ocol, const int32_t *deg,
-                         const uint32_t *t, int64_t n, int64_t m, const int32_t *orows, PruneArgs a, uint32_t *keep,
+                         const uint32_t *t, int64_t n, int64_t m, const int32_t *orows, const int32_t *osrc,
+                         PruneArgs a, uint32_t *keep,
                          int32_t *parent, unsigned long long *ctr, cudaStream_t s);
 cudaError_t launch_prune_seg(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
-                             int64_t n, int64_t m, const int32_t *orows, int measure, const int64_t *sp,
+                             int64_t n, int64_t m, const int32_t *orows, const int32_t *osrc, int measure,
+                             const int64_t *sp,
                              const int64_t *sq, const int64_t *seg_off, int nseg, bool hook, uint32_t *keep,
                              int32_t *parent, unsigned long long *ctr, cudaStream_t s);
 cudaError_t launch_export(const int64_t *off, const int32_t *col, const int32_t *deg,
@@ -220,8 +224,8 @@ cudaError_t launch_snapshot(int32_t *parent, int64_t n, int32_t *labels, const i
 
 // eval.cu: picker features per graph and adjusted Rand index per (level, graph).
 cudaError_t launch_features(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
-                            int64_t n, int64_t m, const int32_t *orows, const int64_t *seg_off, int nseg,
-                            unsigned int *hist, float *feat, unsigned long long *ctr, cudaStream_t s);
+                            int64_t n, int64_t m, const int32_t *orows, const int32_t *osrc, const int64_t *seg_off,
+                            int nseg, unsigned int *hist, float *feat, unsigned long long *ctr, cudaStream_t s);
 int ari_table_bits(int64_t n);
 cudaError_t launch_best_level(const double *ari, int k, int nseg, int32_t *best, double *best_ari, cudaStream_t s);
 // ARI_CHUNK levels share one zeroing of the pair sums (sums holds 2 x nseg x ARI_CHUNK).
@@ -264,8 +268,8 @@ cudaError_t launch_prf(const int32_t *labels, int k, const int32_t *truth, int64
 // cc.cu
 cudaError_t launch_cc_init(int32_t *parent, int64_t n, cudaStream_t s);
 cudaError_t launch_cc_hook(const int64_t *ooff, const int32_t *ocol, const uint32_t *keep,
-                           int64_t n, int64_t m, const int32_t *orows, int32_t *parent, unsigned long long *ctr,
-                           cudaStream_t s);
+                           int64_t n, int64_t m, const int32_t *orows, const int32_t *osrc, int32_t *parent,
+                           unsigned long long *ctr, cudaStream_t s);
 cudaError_t launch_cc_finish(int32_t *parent, int64_t n, int32_t *labels,
                              unsigned long long *ctr, cudaStream_t s);
 
@@ -356,6 +360,13 @@ __device__ __forceinline__ void tile_row_range(const int32_t *trow, const int64_
     }
 }
 
+// Source row of oriented edge j: from the per-edge source table osrc when
+// given (one coalesced load), else by binary search over the tile's rows.
+__device__ __forceinline__ int64_t edge_source(const int32_t *osrc, const int64_t *ooff, int64_t r0, int64_t r1,
+                                               int64_t j) {
+    return osrc ? (int64_t)__ldg(&osrc[j]) : row_search(ooff, r0, r1, j);
+}
+
 // Orientation order: u before v iff (deg u, u) < (deg v, v).
 __device__ __forceinline__ bool rank_less(int32_t du, int64_t u, int32_t dv, int64_t v) {
     return du < dv || (du == dv && u < v);
@@ -428,6 +439,7 @@ struct tec_graph {
     uint32_t *flags = nullptr;
     int32_t *sym_rows = nullptr;    // tile-row table of the symmetric CSR
     int32_t *or_rows = nullptr;     // tile-row table of the oriented CSR
+    int32_t *osrc = nullptr;        // m: source row of every oriented edge (written by the orientation)
     int64_t *tile_cnt = nullptr;
     int64_t *tile_base = nullptr;
     int64_t *bsum = nullptr;

@@ -933,19 +933,19 @@ tec_status tec_sweep(tec_graph *g, tec_measure measure, const int64_t *p, const 
     TEC_CUDA(launch_cc_init(g->parent, g->n, s));
     if (g->n > 0) TEC_CUDA(cudaMemsetAsync(g->best, 0, (size_t)g->n * sizeof(unsigned long long), s));
     TEC_CUDA(cudaMemsetAsync(g->msf_changed, 0, 64 * sizeof(unsigned long long), s));
-    TEC_CUDA(launch_levels(g->ooff, g->ocol, g->deg, cts, g->n, g->m, cmp, g->thr, g->thr + k, k, wide,
+    TEC_CUDA(launch_levels(g->ooff, g->ocol, g->deg, cts, g->n, g->m, g->or_rows, g->osrc, cmp, g->thr, g->thr + k, k, wide,
                            g->lvl, g->best, lu, lv, lk, lc, g->ctr, s));
     for (int round = 0; round < rounds; ++round) {
         const unsigned long long *prev = round > 0 ? g->msf_changed + round - 1 : nullptr;
         if (round > 0)
-            TEC_CUDA(launch_msf_offer(g->ooff, g->ocol, g->lvl, g->n, g->m, g->parent, g->best, lu, lv, lk, lc, prev,
+            TEC_CUDA(launch_msf_offer(g->ooff, g->ocol, g->lvl, g->n, g->m, g->osrc, g->parent, g->best, lu, lv, lk, lc, prev,
                                       g->ctr, s));
-        TEC_CUDA(launch_msf_hook(g->ooff, g->ocol, g->lvl, g->n, g->parent, g->best, prev, g->msf_changed + round,
+        TEC_CUDA(launch_msf_hook(g->ooff, g->ocol, g->osrc, g->lvl, g->n, g->parent, g->best, prev, g->msf_changed + round,
                                  g->ctr, s));
     }
     TEC_CUDA(launch_msf_check(g->msf_changed + rounds - 1, g->ctr, s));
     // offline sweep over the forest edges, highest level first
-    TEC_CUDA(launch_forest_buckets(g->ooff, g->ocol, g->lvl, g->n, g->m, k, g->bucket, g->fu, g->fv, g->ctr, s));
+    TEC_CUDA(launch_forest_buckets(g->ooff, g->ocol, g->lvl, g->n, g->m, g->or_rows, g->osrc, k, g->bucket, g->fu, g->fv, g->ctr, s));
     TEC_CUDA(launch_cc_init(g->parent, g->n, s));
     TEC_CUDA(cudaMemsetAsync(g->sw_ncomp, 0, (size_t)k * nsl * sizeof(unsigned long long), s));
     for (int L = k; L >= 1; --L) {
@@ -995,7 +995,7 @@ tec_status tec_sweep_stats(tec_graph *g, tec_measure measure, const int64_t *p, 
     const uint32_t *cts = nullptr;
     int cmp = (int)measure;
     TEC_TRY(measure_counts(g, (int)measure, &cts, &cmp));
-    TEC_CUDA(launch_sweep_stats(g->ooff, g->ocol, g->deg, cts, g->n, g->m, cmp, g->thr, g->thr + 127, k,
+    TEC_CUDA(launch_sweep_stats(g->ooff, g->ocol, g->deg, cts, g->n, g->m, g->or_rows, g->osrc, cmp, g->thr, g->thr + 127, k,
                                 order.data(), wide, labels, seg_off, nseg, g->st_hist, g->st_cnt_n, g->st_cnt_v, cl,
                                 g->st_sums, stats_out, g->ctr, g->stream));
     return TEC_OK;

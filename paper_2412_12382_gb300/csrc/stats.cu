@@ -39,14 +39,14 @@ __device__ __forceinline__ unsigned long long c_sq(unsigned long long v) { retur
 template <bool WIDE>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_stat_edges(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t, int64_t n, int64_t m,
-             int measure, const int64_t *tp, const int64_t *tq, int k, SortedRows rows, const int32_t *labels,
-             const int64_t *seg_off, int nseg, unsigned long long *hist, unsigned long long *ctr) {
+             const int32_t *orows, const int32_t *osrc, int measure, const int64_t *tp, const int64_t *tq, int k,
+             SortedRows rows, const int32_t *labels, const int64_t *seg_off, int nseg, unsigned long long *hist,
+             unsigned long long *ctr) {
     __shared__ unsigned int s_h[2 * (MAXK + 1)];
     if (graph_bad(ctr)) return;                  // uniform over the grid
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
-    const int64_t klast = min(k0 + TILE, m) - 1;
-    const int64_t r0 = row_search(ooff, 0, n - 1, k0);
-    const int64_t r1 = row_search(ooff, r0, n - 1, klast);
+    int64_t r0, r1;
+    tile_row_range(orows, ooff, n, m, r0, r1);
     int s0 = 0;
     bool one = true;
     if (seg_off) {
@@ -58,7 +58,7 @@ k_stat_edges(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const
     for (int i = 0; i < TILE_ITEMS; ++i) {
         const int64_t j = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
         if (j >= m) break;
-        const int64_t u = row_search(ooff, r0, r1, j);
+        const int64_t u = edge_source(osrc, ooff, r0, r1, j);
         const int32_t v = ocol[j];
         const int64_t s = (int64_t)deg[u] + deg[v];
         const uint32_t tt = t[j];
@@ -297,7 +297,7 @@ SortedRows make_rows(const int *order, int k) {
 }  // namespace
 
 cudaError_t launch_sweep_stats(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
-                               int64_t n, int64_t m, int measure, const int64_t *tp, const int64_t *tq, int k,
+                               int64_t n, int64_t m, const int32_t *orows, const int32_t *osrc, int measure, const int64_t *tp, const int64_t *tq, int k,
                                const int *order, bool wide, const int32_t *labels, const int64_t *seg_off, int nseg,
                                unsigned long long *hist, unsigned int *cnt_n, unsigned long long *cnt_v,
                                int64_t cnt_len, unsigned long long *sums, tec_sweep_stat *out,
@@ -313,11 +313,11 @@ cudaError_t launch_sweep_stats(const int64_t *ooff, const int32_t *ocol, const i
     if (m > 0) {
         const unsigned grid = (unsigned)ceil_div(m, TILE);
         if (wide)
-            k_stat_edges<true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, measure, tp, tq, k, rows, labels,
-                                                             seg_off, ns, hist, ctr);
+            k_stat_edges<true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, osrc, measure, tp, tq, k,
+                                                             rows, labels, seg_off, ns, hist, ctr);
         else
-            k_stat_edges<false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, measure, tp, tq, k, rows,
-                                                              labels, seg_off, ns, hist, ctr);
+            k_stat_edges<false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, osrc, measure, tp, tq,
+                                                              k, rows, labels, seg_off, ns, hist, ctr);
         ++launched;
     }
     for (int r = 0; r < k && n > 0; ++r) {

@@ -63,13 +63,13 @@ __device__ __forceinline__ int block_excl_prefix(int c, int *total) {
 template <bool WIDE, bool COMPACT>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_levels(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t, int64_t n, int64_t m,
-         int measure, const int64_t *tp, const int64_t *tq, int k, uint8_t *lvl, unsigned long long *best,
-         int32_t *lu, int32_t *lv, unsigned long long *lk, int32_t *rcnt, unsigned long long *ctr) {
+         const int32_t *orows, const int32_t *osrc, int measure, const int64_t *tp, const int64_t *tq, int k,
+         uint8_t *lvl, unsigned long long *best, int32_t *lu, int32_t *lv, unsigned long long *lk, int32_t *rcnt,
+         unsigned long long *ctr) {
     if (graph_bad(ctr)) return;                  // uniform over the grid
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
-    const int64_t klast = min(k0 + TILE, m) - 1;
-    const int64_t r0 = row_search(ooff, 0, n - 1, k0);
-    const int64_t r1 = row_search(ooff, r0, n - 1, klast);
+    int64_t r0 = 0, r1 = 0;
+    if (!osrc) tile_row_range(orows, ooff, n, m, r0, r1);
     int32_t eu[TILE_ITEMS], ev[TILE_ITEMS];
     uint8_t el[TILE_ITEMS];
     int c = 0;
@@ -79,7 +79,7 @@ k_levels(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uin
         el[i] = 0;
         eu[i] = ev[i] = 0;
         if (j >= m) continue;
-        const int64_t u = row_search(ooff, r0, r1, j);
+        const int64_t u = edge_source(osrc, ooff, r0, r1, j);
         const int32_t v = ocol[j];
         const int64_t s = (int64_t)deg[u] + deg[v];
         const uint32_t tt = t[j];
@@ -166,7 +166,7 @@ k_msf_offer_list(int32_t *lu, int32_t *lv, unsigned long long *lk, int32_t *rcnt
 
 // Every edge with L >= 1 between two different trees offers itself to both roots.
 __global__ void __launch_bounds__(TILE_THREADS)
-k_msf_offer(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_t n, int64_t m,
+k_msf_offer(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_t n, int64_t m, const int32_t *osrc,
             int32_t *parent, unsigned long long *best, const unsigned long long *prev_changed,
             unsigned long long *ctr) {
     if (*prev_changed == 0ull) return;           // forest complete; uniform over the grid
@@ -174,14 +174,17 @@ k_msf_offer(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t k0 = tile * TILE;
         const int64_t klast = min(k0 + TILE, m) - 1;
-        const int64_t r0 = row_search(ooff, 0, n - 1, k0);
-        const int64_t r1 = row_search(ooff, r0, n - 1, klast);
+        int64_t r0 = 0, r1 = 0;
+        if (!osrc) {
+            r0 = row_search(ooff, 0, n - 1, k0);
+            r1 = row_search(ooff, r0, n - 1, klast);
+        }
         for (int i = 0; i < TILE_ITEMS; ++i) {
             const int64_t j = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
             if (j >= m) break;
             const uint8_t L = lvl[j] & (uint8_t)~FOREST_BIT;
             if (L == 0) continue;
-            const int32_t u = (int32_t)row_search(ooff, r0, r1, j);
+            const int32_t u = (int32_t)edge_source(osrc, ooff, r0, r1, j);
             const int32_t ru = uf_find(parent, u), rv = uf_find(parent, ocol[j]);
             if (ru == rv) continue;
             const uint64_t key = msf_key(L, j);
@@ -195,8 +198,8 @@ k_msf_offer(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_
 // forest edge and sets this round's changed flag (one store per block).
 // Clears the offers for the next round.  Skipped when the previous round
 // joined nothing (the forest is complete).
-__global__ void k_msf_hook(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int32_t *parent,
-                           unsigned long long *best, const unsigned long long *prev_changed,
+__global__ void k_msf_hook(const int64_t *ooff, const int32_t *ocol, const int32_t *osrc, uint8_t *lvl, int64_t n,
+                           int32_t *parent, unsigned long long *best, const unsigned long long *prev_changed,
                            unsigned long long *changed, unsigned long long *ctr) {
     if (prev_changed && *prev_changed == 0ull) return;   // uniform over the grid
     int did = 0;
@@ -205,7 +208,7 @@ __global__ void k_msf_hook(const int64_t *ooff, const int32_t *ocol, uint8_t *lv
         if (!key) continue;
         best[r] = 0ull;
         const int64_t j = msf_key_edge(key);
-        const int32_t u = (int32_t)row_search(ooff, 0, n - 1, j);
+        const int32_t u = osrc ? osrc[j] : (int32_t)row_search(ooff, 0, n - 1, j);
         if (uf_link_merged(parent, u, ocol[j], ctr)) {
             lvl[j] |= FOREST_BIT;
             did = 1;
@@ -259,8 +262,9 @@ __global__ void k_forest_offsets(unsigned long long *bucket, int k, int64_t n, u
 // per-level counts are reserved with one global atomic per level, then each
 // edge takes a slot from a shared-memory cursor.
 __global__ void __launch_bounds__(TILE_THREADS)
-k_forest_scatter(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_t n, int64_t m, int k,
-                 unsigned long long *bucket, int32_t *fu, int32_t *fv) {
+k_forest_scatter(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_t n, int64_t m,
+                 const int32_t *orows, const int32_t *osrc, int k, unsigned long long *bucket, int32_t *fu,
+                 int32_t *fv) {
     __shared__ unsigned int cnt[128];
     __shared__ unsigned long long base[128];
     for (int b = threadIdx.x; b <= k; b += blockDim.x) cnt[b] = 0;
@@ -277,9 +281,8 @@ k_forest_scatter(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, i
         cnt[b] = 0;
     }
     __syncthreads();
-    const int64_t klast = min(k0 + TILE, m) - 1;
-    const int64_t r0 = row_search(ooff, 0, n - 1, k0);
-    const int64_t r1 = row_search(ooff, r0, n - 1, klast);
+    int64_t r0 = 0, r1 = 0;
+    if (!osrc) tile_row_range(orows, ooff, n, m, r0, r1);
     for (int i = 0; i < TILE_ITEMS; ++i) {
         const int64_t j = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
         if (j >= m) break;
@@ -287,7 +290,7 @@ k_forest_scatter(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, i
         const int L = lvl[j] & (uint8_t)~FOREST_BIT;
         const unsigned long long at = base[L] + atomicAdd(&cnt[L], 1u);
         if (at >= (unsigned long long)n) continue;   // a forest has < n edges; the host checks the total
-        fu[at] = (int32_t)row_search(ooff, r0, r1, j);
+        fu[at] = (int32_t)edge_source(osrc, ooff, r0, r1, j);
         fv[at] = ocol[j];
     }
 }
@@ -389,15 +392,16 @@ unsigned vertex_pass_grid(int64_t n) {
 }
 
 cudaError_t launch_levels(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
-                          int64_t n, int64_t m, int measure, const int64_t *tp, const int64_t *tq, int k, bool wide,
+                          int64_t n, int64_t m, const int32_t *orows, const int32_t *osrc, int measure,
+                          const int64_t *tp, const int64_t *tq, int k, bool wide,
                           uint8_t *lvl, unsigned long long *best, int32_t *lu, int32_t *lv, unsigned long long *lk,
                           int32_t *rcnt, unsigned long long *ctr, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)ceil_div(m, TILE);
     const bool compact = lu != nullptr;
 #define TEC_LEVELS(W, C) \
-    k_levels<W, C><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, measure, tp, tq, k, lvl, best, lu, lv, lk, \
-                                                 rcnt, ctr)
+    k_levels<W, C><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, osrc, measure, tp, tq, k, lvl, \
+                                                 best, lu, lv, lk, rcnt, ctr)
     if (wide) {
         if (compact) TEC_LEVELS(true, true); else TEC_LEVELS(true, false);
     } else {
@@ -409,7 +413,7 @@ cudaError_t launch_levels(const int64_t *ooff, const int32_t *ocol, const int32_
 }
 
 cudaError_t launch_msf_offer(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int64_t m,
-                             int32_t *parent, unsigned long long *best, int32_t *lu, int32_t *lv,
+                             const int32_t *osrc, int32_t *parent, unsigned long long *best, int32_t *lu, int32_t *lv,
                              unsigned long long *lk, int32_t *rcnt, const unsigned long long *prev_changed,
                              unsigned long long *ctr, cudaStream_t s) {
     if (m <= 0 || n <= 0) return cudaSuccess;
@@ -419,16 +423,16 @@ cudaError_t launch_msf_offer(const int64_t *ooff, const int32_t *ocol, uint8_t *
     if (lu)
         k_msf_offer_list<<<grid, TILE_THREADS, 0, s>>>(lu, lv, lk, rcnt, ntiles, parent, best, prev_changed);
     else
-        k_msf_offer<<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, lvl, n, m, parent, best, prev_changed, ctr);
+        k_msf_offer<<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, lvl, n, m, osrc, parent, best, prev_changed, ctr);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_msf_hook(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int32_t *parent,
-                            unsigned long long *best, const unsigned long long *prev_changed,
+cudaError_t launch_msf_hook(const int64_t *ooff, const int32_t *ocol, const int32_t *osrc, uint8_t *lvl, int64_t n,
+                            int32_t *parent, unsigned long long *best, const unsigned long long *prev_changed,
                             unsigned long long *changed, unsigned long long *ctr, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_msf_hook<<<vertex_pass_grid(n), 256, 0, s>>>(ooff, ocol, lvl, n, parent, best, prev_changed, changed, ctr);
+    k_msf_hook<<<vertex_pass_grid(n), 256, 0, s>>>(ooff, ocol, osrc, lvl, n, parent, best, prev_changed, changed, ctr);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -448,7 +452,7 @@ cudaError_t launch_store_thresholds(const int64_t *sorted_pq, int count, int64_t
 }
 
 cudaError_t launch_forest_buckets(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_t n, int64_t m,
-                                  int k, unsigned long long *bucket, int32_t *fu, int32_t *fv, unsigned long long *ctr,
+                                  const int32_t *orows, const int32_t *osrc, int k, unsigned long long *bucket, int32_t *fu, int32_t *fv, unsigned long long *ctr,
                                   cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(bucket, 0, (size_t)(k + 1) * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
@@ -456,7 +460,8 @@ cudaError_t launch_forest_buckets(const int64_t *ooff, const int32_t *ocol, cons
     if (m > 0) k_forest_count<<<(unsigned)(cblocks < 152 * 16 ? cblocks : 152 * 16), 256, 0, s>>>(lvl, m, k, bucket);
     k_forest_offsets<<<1, 1, 0, s>>>(bucket, k, n, ctr);
     if (m > 0)
-        k_forest_scatter<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, lvl, n, m, k, bucket, fu, fv);
+        k_forest_scatter<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, lvl, n, m, orows, osrc, k, bucket,
+                                                                                    fu, fv);
     count_launches(m > 0 ? 3 : 1);
     return cudaGetLastError();
 }

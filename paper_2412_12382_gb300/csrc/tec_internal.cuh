@@ -193,18 +193,20 @@ cudaError_t launch_upper_counts(const int64_t *off, const int32_t *col, int64_t 
 // must be zero); with lu != nullptr also the live-edge list for later rounds
 // (lu, lv, lk with ceil(m / TILE) * TILE entries, rcnt one count per tile).
 cudaError_t launch_levels(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
-                          int64_t n, int64_t m, int measure, const int64_t *tp, const int64_t *tq, int k, bool wide,
+                          int64_t n, int64_t m, const int32_t *orows, const int32_t *osrc, int measure,
+                          const int64_t *tp, const int64_t *tq, int k, bool wide,
                           uint8_t *lvl, unsigned long long *best, int32_t *lu, int32_t *lv, unsigned long long *lk,
                           int32_t *rcnt, unsigned long long *ctr, cudaStream_t s);
 // A later Boruvka round's offers: from the live-edge list if lu != nullptr,
 // else from the CSR; nothing when *prev_changed is 0 (the forest is complete).
 cudaError_t launch_msf_offer(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int64_t m,
-                             int32_t *parent, unsigned long long *best, int32_t *lu, int32_t *lv,
+                             const int32_t *osrc, int32_t *parent, unsigned long long *best, int32_t *lu, int32_t *lv,
                              unsigned long long *lk, int32_t *rcnt, const unsigned long long *prev_changed,
                              unsigned long long *ctr, cudaStream_t s);
 // Hooks every root along its heaviest offer, clears the offers and sets
 // *changed when a tree grew; nothing when prev_changed is set and 0.
-cudaError_t launch_msf_hook(const int64_t *ooff, const int32_t *ocol, uint8_t *lvl, int64_t n, int32_t *parent,
+cudaError_t launch_msf_hook(const int64_t *ooff, const int32_t *ocol, const int32_t *osrc, uint8_t *lvl, int64_t n,
+                            int32_t *parent,
                             unsigned long long *best, const unsigned long long *prev_changed,
                             unsigned long long *changed, unsigned long long *ctr, cudaStream_t s);
 // Flags TEC_ETIMEOUT if the last allowed round still grew the forest.
@@ -212,7 +214,7 @@ cudaError_t launch_msf_check(const unsigned long long *last_changed, unsigned lo
 // Stores count int64 values (sorted p then q) to dst from the launch parameters.
 cudaError_t launch_store_thresholds(const int64_t *sorted_pq, int count, int64_t *dst, cudaStream_t s);
 cudaError_t launch_forest_buckets(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_t n, int64_t m,
-                                  int k, unsigned long long *bucket, int32_t *fu, int32_t *fv, unsigned long long *ctr,
+                                  const int32_t *orows, const int32_t *osrc, int k, unsigned long long *bucket, int32_t *fu, int32_t *fv, unsigned long long *ctr,
                                   cudaStream_t s);
 // Unions level L's bucket (bounds read on the device), then snapshots the labels.
 cudaError_t launch_sweep_level(const int32_t *fu, const int32_t *fv, const unsigned long long *bucket, int k, int L,
@@ -243,7 +245,7 @@ cudaError_t launch_ari(const int32_t *labels, int k, const int32_t *truth, int64
 // = row of the i-th; hist 2 (k+1) per graph, sums 3 per row and graph,
 // cnt_n / cnt_v two arrays of cnt_len >= n each).
 cudaError_t launch_sweep_stats(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t,
-                               int64_t n, int64_t m, int measure, const int64_t *tp, const int64_t *tq, int k,
+                               int64_t n, int64_t m, const int32_t *orows, const int32_t *osrc, int measure, const int64_t *tp, const int64_t *tq, int k,
                                const int *order, bool wide, const int32_t *labels, const int64_t *seg_off, int nseg,
                                unsigned long long *hist, unsigned int *cnt_n, unsigned long long *cnt_v,
                                int64_t cnt_len, unsigned long long *sums, tec_sweep_stat *out,

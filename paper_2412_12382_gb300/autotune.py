@@ -166,9 +166,12 @@ def time_variant(lib: str, cmd: str, metric: str, reps: int, cwd: str) -> float:
     return statistics.median(values)
 
 
-def coordinate_descent(space: dict, start: dict, evaluate, lower_is_better: bool = True, max_rounds: int = 4):
+def coordinate_descent(space: dict, start: dict, evaluate, lower_is_better: bool = True, max_rounds: int = 4,
+                       min_gain: float = 0.0):
     """Coordinate descent over `space` (name -> candidates) from `start`.
-    evaluate(point) returns a cost, or None for a point that cannot run.
+    evaluate(point) returns a cost, or None for a point that cannot run.  A
+    move is taken only when it improves the cost by more than the fraction
+    `min_gain` (differences within one run's noise do not change constants).
     Returns (best point, best cost, {point key: cost})."""
     seen = {}
 
@@ -183,7 +186,7 @@ def coordinate_descent(space: dict, start: dict, evaluate, lower_is_better: bool
             return False
         if b is None:
             return True
-        return a < b if lower_is_better else a > b
+        return a < b * (1.0 - min_gain) if lower_is_better else a > b * (1.0 + min_gain)
 
     best = dict(start)
     best_cost = cost(best)
@@ -209,7 +212,7 @@ def check_variant(lib: str, check_cmd: str, cwd: str) -> bool:
 
 
 def tune(params, cmd, metric, reps=3, lower_is_better=True, cache_path=None, device="", cwd=None, log=print,
-         check_cmd=None, size_class=""):
+         check_cmd=None, size_class="", min_gain=0.005):
     cwd = cwd or os.path.dirname(HERE)
     texts = {f: open(os.path.join(_build.CSRC, f)).read() for f in {TUNABLES[p][0] for p in params}}
     start = {p: int_value(current_value(texts[TUNABLES[p][0]], p)) for p in params}
@@ -250,7 +253,7 @@ def tune(params, cmd, metric, reps=3, lower_is_better=True, cache_path=None, dev
                 json.dump(cache, f, indent=1, sort_keys=True)
         return entries[pk]
 
-    best, best_cost, _ = coordinate_descent(space, start, evaluate, lower_is_better)
+    best, best_cost, _ = coordinate_descent(space, start, evaluate, lower_is_better, min_gain=min_gain)
     return start, best, best_cost, entries
 
 
@@ -265,6 +268,9 @@ def main(argv=None):
                          "'python -m pytest tests/test_gpu_parity.py -m gpu -x -q'")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--cache", default="autotune_cache.json")
+    ap.add_argument("--min-gain", type=float, default=0.005,
+                    help="smallest relative improvement that changes a constant (default 0.5%%, about one run's "
+                         "noise on the scale-26 triangle stage)")
     ap.add_argument("--size-class", default="",
                     help="label of the workload's size class (e.g. rmat26, rmat22, dcsbm256): the best "
                          "constants differ between classes, so each has its own cache entries")
@@ -278,7 +284,8 @@ def main(argv=None):
     except ImportError:
         pass
     start, best, cost, _ = tune(params, args.cmd, args.metric, args.reps, not args.higher_is_better,
-                                args.cache, device, check_cmd=args.check_cmd, size_class=args.size_class)
+                                args.cache, device, check_cmd=args.check_cmd, size_class=args.size_class,
+                                min_gain=args.min_gain)
     print(json.dumps({"start": start, "best": best, "cost": cost, "metric": args.metric,
                       "size_class": args.size_class}))
     return 0

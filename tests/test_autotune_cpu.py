@@ -116,3 +116,28 @@ def test_library_override_is_only_for_loading(monkeypatch):
     monkeypatch.setenv("TEC_LIBRARY", "/nonexistent/variant.so")
     assert B.library_path() == "/nonexistent/variant.so"
     assert B.default_library_path().endswith(os.path.join("_build", "libtectonic.so"))
+
+
+def test_descent_ignores_gains_within_noise():
+    # a 0.1% better neighbour does not move the constants at min_gain = 0.5%, a 2% better one does
+    costs = {(16, 16): 100.0, (12, 16): 99.9, (16, 12): 100.05, (12, 12): 99.9}
+    space = {"A": [12, 16], "B": [12, 16]}
+    ev = lambda p: costs[(p["A"], p["B"])]
+    best, cost, _ = A.coordinate_descent(space, {"A": 16, "B": 16}, ev, min_gain=0.005)
+    assert best == {"A": 16, "B": 16} and cost == 100.0
+    costs[(12, 16)] = 98.0
+    best, cost, _ = A.coordinate_descent(space, {"A": 16, "B": 16}, ev, min_gain=0.005)
+    assert best["A"] == 12 and cost == 98.0
+
+
+def test_shipped_cache_records_the_gpu_run():
+    """The committed cache holds the scale-26 run on a GB300: every point of
+    the descent with its triangle-stage time, keyed by device and size class."""
+    path = os.path.join(os.path.dirname(A.__file__), "autotune_cache.json")
+    cache = json.load(open(path))
+    keys = [json.loads(k) for k in cache]
+    k26 = [k for k in keys if k.get("size_class") == "rmat26"]
+    assert k26 and k26[0]["device"] == "NVIDIA GB300" and k26[0]["metric"] == "config.stage_ms.support"
+    entries = cache[json.dumps(k26[0])] if json.dumps(k26[0]) in cache else next(iter(cache.values()))
+    times = [v for v in entries.values() if v is not None]
+    assert len(times) >= 9 and min(times) > 0

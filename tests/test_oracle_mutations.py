@@ -113,6 +113,11 @@ MLP_MUTANTS = [
      "loss gradient without the factor 2"),
     ("mhat = m / (1 - beta1 ** step)", "mhat = m",
      "Adam without the first-moment bias correction"),
+    ("dval = 64.0 / (sigma * sigma) * ((w * L * d).sum(axis=1) - val * (w * d).sum(axis=1))",
+     "dval = 64.0 / (sigma * sigma) * (w * L * d).sum(axis=1)",
+     "soft-level loss derivative without the normalisation term"),
+    ("d = i[None, :] - 64.0 * y[:, None]", "d = i[None, :] - 63.0 * y[:, None]",
+     "soft-level loss centred on 63 y instead of 64 y"),
 ]
 
 

@@ -4,7 +4,9 @@
 
 Training graphs: degree-corrected SBM graphs of seeds 10000-19999 with
 n in [1000, 100000]; 10% of them (every tenth seed) are a validation split
-that picks the epoch count kept.  Held-out evaluation: seeds 20000-20499.
+that picks the epoch count kept.  With --refit the network is then trained
+again from the same initialisation on all 10,000 graphs for that epoch
+count.  Held-out evaluation: seeds 20000-20499.
 Labels: the grid threshold b/128 (b = 1..64) of highest ARI against the
 planted blocks, from the full sweep.  Everything runs in the library's
 kernels; this script only orders the calls.
@@ -38,6 +40,10 @@ def main(argv=None):
     ap.add_argument("--train-seeds", type=int, nargs=2, default=(10000, 20000))
     ap.add_argument("--eval-seeds", type=int, nargs=2, default=(20000, 20500))
     ap.add_argument("--n-range", type=int, nargs=2, default=(1000, 100000))
+    ap.add_argument("--refit", action="store_true",
+                    help="after choosing the epoch count on the validation split, train again from the same "
+                         "initialisation on all training graphs (validation split included) for that many "
+                         "epochs, and keep that network")
     ap.add_argument("--dataset-cache", default=None,
                     help="directory for the labelled datasets (features + best levels), reused by later runs")
     args = ap.parse_args(argv)
@@ -65,16 +71,29 @@ def main(argv=None):
     t_train = time.time() - t1
     params, m, v, step = best[1]
     pk.set_params(params, m, v, step)
+    epochs_run = done
+    refit = None
+    if args.refit:
+        import torch
+        full = {k: torch.cat([train[k], val[k]], dim=1 if k == "ari" else 0) for k in P.DATASET_FIELDS}
+        pk.free()
+        pk = P.T.Picker(P.init_params(0))
+        done = 0
+        while done < best[2]:
+            e = min(args.chunk, best[2] - done)
+            losses += pk.train(full["feats"], full["target"], e, args.batch, args.lr, seed=done + 1).tolist()
+            done += e
+        refit = {"graphs": int(full["feats"].shape[0]), "epochs": best[2]}
     fixed = P.fixed_level(train)
     res = P.evaluate(pk, held, baseline_level=fixed)
     res_bf16 = P.evaluate(pk, held, bf16=True)
     agree = float((P.predict_levels(pk, held["feats"], False) == P.predict_levels(pk, held["feats"], True))
                   .float().mean().item())
     meta = {"train_seeds": [tr_seeds[0], tr_seeds[-1], len(tr_seeds)], "val_seeds": len(val_seeds),
-            "eval_seeds": list(args.eval_seeds), "n_range": list(args.n_range), "epochs_run": done,
+            "eval_seeds": list(args.eval_seeds), "n_range": list(args.n_range), "epochs_run": epochs_run,
             "epochs_kept": best[2], "val_mean_dARI": best[0], "lr": args.lr, "batch": args.batch,
             "final_train_loss": losses[-1], "first_train_loss": losses[0], "eval": res,
-            "eval_bf16": res_bf16, "bf16_same_level_fraction": agree,
+            "eval_bf16": res_bf16, "bf16_same_level_fraction": agree, "refit": refit,
             "seconds": {"data": t_data, "train": t_train}}
     P.save(pk, args.out, meta)
     print(json.dumps(meta))

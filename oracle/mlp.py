@@ -51,12 +51,8 @@ def loss(theta, X, target):
     return float(np.mean((y - np.asarray(target, dtype=np.float64)) ** 2))
 
 
-def loss_and_grad(theta, X, target):
-    """Loss and its gradient by the chain rule (backpropagation)."""
-    p = unpack(theta)
-    y, (X, z1, h1, z2, h2) = forward(theta, X)
-    n = X.shape[0]
-    dy = 2.0 * (y - np.asarray(target, dtype=np.float64)) / n
+def _backprop(p, dy, X, z1, h1, z2, h2):
+    """Gradient of every parameter from dloss/dy by the chain rule."""
     g = {"w3": h2.T @ dy, "b3": np.array([dy.sum()])}
     dz2 = np.outer(dy, p["w3"]) * (z2 > 0)
     g["W2"] = dz2.T @ h1
@@ -64,7 +60,16 @@ def loss_and_grad(theta, X, target):
     dz1 = (dz2 @ p["W2"]) * (z1 > 0)
     g["W1"] = dz1.T @ X
     g["b1"] = dz1.sum(0)
-    return float(np.mean((y - target) ** 2)), pack(g)
+    return pack(g)
+
+
+def loss_and_grad(theta, X, target):
+    """Loss and its gradient by the chain rule (backpropagation)."""
+    p = unpack(theta)
+    y, (X, z1, h1, z2, h2) = forward(theta, X)
+    n = X.shape[0]
+    dy = 2.0 * (y - np.asarray(target, dtype=np.float64)) / n
+    return float(np.mean((y - target) ** 2)), _backprop(p, dy, X, z1, h1, z2, h2)
 
 
 def soft_level_loss(y, L, sigma):
@@ -96,14 +101,7 @@ def mixed_loss_and_grad(theta, X, target, L, sigma, mix):
     t = np.asarray(target, dtype=np.float64)
     sv, sd = soft_level_loss(y, L, sigma)
     dy = (mix * 2.0 * (y - t) + (1.0 - mix) * sd) / n
-    g = {"w3": h2.T @ dy, "b3": np.array([dy.sum()])}
-    dz2 = np.outer(dy, p["w3"]) * (z2 > 0)
-    g["W2"] = dz2.T @ h1
-    g["b2"] = dz2.sum(0)
-    dz1 = (dz2 @ p["W2"]) * (z1 > 0)
-    g["W1"] = dz1.T @ X
-    g["b1"] = dz1.sum(0)
-    return float(np.mean(mix * (y - t) ** 2 + (1.0 - mix) * sv)), pack(g)
+    return float(np.mean(mix * (y - t) ** 2 + (1.0 - mix) * sv)), _backprop(p, dy, X, z1, h1, z2, h2)
 
 
 def adam(theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):

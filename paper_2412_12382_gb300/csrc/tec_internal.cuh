@@ -301,7 +301,7 @@ __device__ __forceinline__ int warp_seg_of(const int64_t *seg_off, int nseg, int
 // Vertex passes (snapshot, ARI) hand each warp chunks of VCHUNK_V x 32
 // consecutive vertices: one segment lookup per chunk, VCHUNK_V independent
 // loads in flight per lane.
-constexpr int VCHUNK_V = 8;
+constexpr int VCHUNK_V = 4;
 constexpr int VCHUNK = 32 * VCHUNK_V;
 
 // Grid for a persistent vertex pass of 256-thread blocks: enough warps for

@@ -66,6 +66,13 @@ def test_null_arguments_rejected_without_touching_a_device(lib):
     assert L.tec_set_core_staging(None, 1) == 1
     assert L.tec_prune_components_batch(None, 0, None, None, None, 0, None, None) == 1
     assert L.tec_picker_thresholds(None, -1, None, None, None) == 1
+    assert L.tec_set_support_tiling(None, 0) == 1
+    assert L.tec_picker_file_write(None, None, None, None, 0, None) == 1
+    assert L.tec_picker_file_read(None, None, None, None, None, None, 0, None) == 1
+    assert L.tec_picker_save(None, b"x", None) == 1
+    assert L.tec_picker_load(None, None, None) == 1
+    assert L.tec_picker_train_soft(None, None, None, None, 0, 1, 1, 1e-3, 0, 1.0, 0.5, None) == 1
+    assert L.tec_picker_soft_loss_grad(None, None, None, None, 0, 1.0, 0.5, None, None) == 1
 
 
 def test_binding_fails_loudly_without_gpu():

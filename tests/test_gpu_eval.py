@@ -54,6 +54,30 @@ def test_features_single_and_batch(tec):
     g.free()
 
 
+def test_feature_bin_counts_are_exact(tec):
+    """The 64 bins are integer counts divided by m in float32; for these
+    sizes (m < 2^22) round(f m) recovers each count exactly, and it must equal
+    the oracle's integer histogram bin for bin: a count off by one would move
+    the float by only 1/m."""
+    import torch
+    from graphgen.dcsbm import dcsbm_csr
+    graphs = [planted_partition(4, 500, 0.05, 0.002, seed=1)[:2], rmat_csr(14, 16, seed=4),
+              dcsbm_csr(20003, 1000, 100000)[:2], small.two_cliques_bridge(6, 9)]
+    off, col, seg = disjoint_union(graphs)
+    g = _graph(tec, off, col)
+    f = g.features(torch.from_numpy(seg).cuda()).cpu().numpy()
+    for i, (go, gc) in enumerate(graphs):
+        eu, ev = O.edge_list(go, gc)
+        t, _ = O.edge_counts(go, gc, eu, ev, nthreads=O.threads_available())
+        h = O.histogram64(go, eu, ev, t)
+        m = len(eu)
+        assert m < (1 << 22)
+        counts = np.rint(f[i][:64].astype(np.float64) * m).astype(np.int64)
+        assert np.array_equal(counts, h), i
+        assert counts.sum() == m
+    g.free()
+
+
 def test_ari_of_sweep_against_planted_blocks(tec):
     import torch
     sizes = [[60, 80, 50], [120, 40], [30] * 6]

@@ -5,7 +5,9 @@
 // every oriented row stays sorted, and the oriented offset of row u is the
 // number of kept entries before off[u].  Two streaming passes over tiles of
 // 2048 entries: (1) keep bits + per-tile counts, (2) after a scan of the tile
-// counts, scatter of the kept ids and of the row offsets.
+// counts, scatter of the kept ids and of the row offsets.  Each tile learns
+// the row of its entries from one coalesced read of its rows' offsets
+// (tile_entry_rows).
 #include "tec_internal.cuh"
 
 namespace tec {
@@ -49,13 +51,16 @@ __global__ void k_validate_rows(const int64_t *off, int64_t n, int64_t nnz, unsi
 __global__ void __launch_bounds__(TILE_THREADS)
 k_validate_entries(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz, const int32_t *trow,
                    unsigned long long *ctr) {
+    __shared__ __align__(16) int32_t s_row[TILE];
+    __shared__ int32_t s_warp[TILE_THREADS / 32];
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
     int64_t r0, r1;
     tile_row_range(trow, off, n, nnz, r0, r1);
+    tile_entry_rows(off, nnz, r0, r1, s_row, s_warp);
     for (int i = 0; i < TILE_ITEMS; ++i) {
         int64_t k = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
         if (k >= nnz) break;
-        int64_t u = row_search(off, r0, r1, k);
+        int64_t u = r0 + s_row[i * TILE_THREADS + threadIdx.x];
         int64_t v = col[k];
         bool bad = v < 0 || v >= n || v == u || (k > off[u] && col[k - 1] >= v);
         if (!bad) {
@@ -82,25 +87,45 @@ __device__ __forceinline__ int block_sum_int(int x) {
     return tot;
 }
 
-// Pass 1: keep bit per symmetric entry (bit k of flags) and kept count per tile.
+// Pass 1: keep bit per symmetric entry (bit k of flags) and kept count per
+// tile.  The column ids of all eight items are loaded before the row pass
+// and every degree gather is issued before any is used, so each thread keeps
+// several loads in flight.
 __global__ void __launch_bounds__(TILE_THREADS)
-k_orient_flags(const int64_t *off, const int32_t *col, const int32_t *deg, int64_t n, int64_t nnz,
-               const int32_t *trow, uint32_t *flags, int64_t *tile_cnt, unsigned long long *ctr) {
+k_orient_flags(const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ deg,
+               int64_t n, int64_t nnz, const int32_t *__restrict__ trow, uint32_t *__restrict__ flags,
+               int64_t *__restrict__ tile_cnt, unsigned long long *ctr) {
+    __shared__ __align__(16) int32_t s_row[TILE];
+    __shared__ int32_t s_warp[TILE_THREADS / 32];
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
     int64_t r0, r1;
     tile_row_range(trow, off, n, nnz, r0, r1);
+    int32_t v[TILE_ITEMS];
+#pragma unroll
+    for (int i = 0; i < TILE_ITEMS; ++i) {
+        const int64_t k = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
+        v[i] = k < nnz ? col[k] : 0;
+    }
+    tile_entry_rows(off, nnz, r0, r1, s_row, s_warp);
+    int32_t du[TILE_ITEMS], dv[TILE_ITEMS];
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < TILE_ITEMS; ++i) {
+        const int64_t k = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
+        const bool in = k < nnz && v[i] >= 0 && (int64_t)v[i] < n;
+        bad |= k < nnz && !in;
+        du[i] = in ? deg[r0 + s_row[i * TILE_THREADS + threadIdx.x]] : 0;
+        dv[i] = in ? deg[v[i]] : 0;
+    }
+    if (bad) flag_status(ctr, ST_BADGRAPH);
     int cnt = 0;
+#pragma unroll
     for (int i = 0; i < TILE_ITEMS; ++i) {
         const int64_t kw = k0 + (int64_t)i * TILE_THREADS + (threadIdx.x & ~31u);
         const int64_t k = kw + lane_id();
-        bool f = false;
-        if (k < nnz) {
-            int64_t u = row_search(off, r0, r1, k);
-            int32_t v = col[k];
-            if (v < 0 || (int64_t)v >= n) flag_status(ctr, ST_BADGRAPH);
-            else f = rank_less(deg[u], u, deg[v], v);
-        }
-        unsigned b = __ballot_sync(0xffffffffu, f);
+        const int64_t u = r0 + s_row[i * TILE_THREADS + threadIdx.x];
+        const bool f = k < nnz && v[i] >= 0 && (int64_t)v[i] < n && rank_less(du[i], u, dv[i], v[i]);
+        const unsigned b = __ballot_sync(0xffffffffu, f);
         if (lane_id() == 0 && kw < nnz) flags[kw >> 5] = b;
         cnt += f ? 1 : 0;
     }
@@ -108,50 +133,75 @@ k_orient_flags(const int64_t *off, const int32_t *col, const int32_t *deg, int64
     if (threadIdx.x == 0) tile_cnt[blockIdx.x] = tot;
 }
 
-// Pass 2: scatter kept ids to ocol[global rank of the keep bit] and write
-// ooff[u] for every row that starts (or, if empty, sits) at an entry of this tile.
+// Pass 2: scatter kept ids to ocol[global rank of the keep bit] (and the
+// source row to osrc) and write ooff[u] for every row that starts (or, if
+// empty, sits) at an entry of this tile.  The rank of a keep bit is the
+// tile's base plus a popcount prefix of the tile's 64 flag words, kept in
+// shared memory; there is no per-item barrier.
 __global__ void __launch_bounds__(TILE_THREADS)
-k_orient_fill(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz, const int32_t *trow,
-              const uint32_t *flags, const int64_t *tile_base, int64_t *ooff, int32_t *ocol, int32_t *osrc, int64_t m,
-              unsigned long long *ctr) {
-    __shared__ int s_wc[TILE_THREADS / 32];
+k_orient_fill(const int64_t *__restrict__ off, const int32_t *__restrict__ col, int64_t n, int64_t nnz,
+              const int32_t *__restrict__ trow, const uint32_t *__restrict__ flags,
+              const int64_t *__restrict__ tile_base, int64_t *__restrict__ ooff, int32_t *__restrict__ ocol,
+              int32_t *__restrict__ osrc, int64_t m, unsigned long long *ctr) {
+    constexpr int WORDS = TILE / 32;
+    __shared__ __align__(16) int32_t s_row[TILE];
+    __shared__ int32_t s_warp[TILE_THREADS / 32];
+    __shared__ uint32_t s_word[WORDS];
+    __shared__ int32_t s_wpre[WORDS];
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
     int64_t r0, r1;
     tile_row_range(trow, off, n, nnz, r0, r1);
-    const unsigned lane = lane_id();
-    const int w = threadIdx.x >> 5;
-    int64_t carry = tile_base[blockIdx.x];
-    for (int i = 0; i < TILE_ITEMS; ++i) {
-        const int64_t kw = k0 + (int64_t)i * TILE_THREADS + w * 32;
-        const int64_t k = kw + lane;
-        const uint32_t word = kw < nnz ? flags[kw >> 5] : 0u;
-        const int wpre = __popc(word & ((1u << lane) - 1u));
-        if (lane == 0) s_wc[w] = __popc(word);
-        __syncthreads();
-        int before = 0, total = 0;
+    const int64_t base = tile_base[blockIdx.x];
+    int32_t c[TILE_ITEMS];
 #pragma unroll
-        for (int x = 0; x < TILE_THREADS / 32; ++x) {
-            before += x < w ? s_wc[x] : 0;
-            total += s_wc[x];
+    for (int i = 0; i < TILE_ITEMS; ++i) {
+        const int64_t k = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
+        c[i] = k < nnz ? col[k] : 0;
+    }
+    if (threadIdx.x < WORDS) {
+        const int64_t kw = k0 + (int64_t)threadIdx.x * 32;
+        s_word[threadIdx.x] = kw < nnz ? flags[kw >> 5] : 0u;
+    }
+    tile_entry_rows(off, nnz, r0, r1, s_row, s_warp);    // its barriers publish s_word
+    static_assert(WORDS == 64, "two flag words per lane of warp 0");
+    if (threadIdx.x < 32) {
+        const int a = __popc(s_word[2 * threadIdx.x]), b = __popc(s_word[2 * threadIdx.x + 1]);
+        int inc = a + b;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, inc, d);
+            if (threadIdx.x >= (unsigned)d) inc += x;
         }
-        const int64_t pos = carry + before + wpre;
-        if (k < nnz) {
-            int64_t u = row_search(off, r0, r1, k);
-            if (off[u] == k) {
-                ooff[u] = pos;
-                for (int64_t x = u - 1; x >= 0 && off[x] == k; --x) ooff[x] = pos;
-            }
-            if ((word >> lane) & 1u) {
-                if (pos < m) {
-                    ocol[pos] = col[k];
-                    if (osrc) osrc[pos] = (int32_t)u;
-                } else {
-                    flag_status(ctr, ST_BADGRAPH);
-                }
+        s_wpre[2 * threadIdx.x] = inc - a - b;
+        s_wpre[2 * threadIdx.x + 1] = inc - b;
+    }
+    __syncthreads();
+    const int64_t k1 = k0 + TILE < nnz ? k0 + TILE : nnz;
+    // oriented offsets of the rows whose first entry lies in the tile
+    for (int64_t r = r0 + threadIdx.x; r <= r1; r += TILE_THREADS) {
+        const int64_t a = off[r];
+        if (a >= k0 && a < k1) {
+            const int p = (int)(a - k0);
+            ooff[r] = base + s_wpre[p >> 5] + __popc(s_word[p >> 5] & ((1u << (p & 31)) - 1u));
+        }
+    }
+    // empty rows just before r0 that sit at the tile's first entry
+    if (threadIdx.x == 0 && off[r0] == k0)
+        for (int64_t x = r0 - 1; x >= 0 && off[x] == k0; --x) ooff[x] = base;
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int i = 0; i < TILE_ITEMS; ++i) {
+        const int p = i * TILE_THREADS + (int)threadIdx.x;
+        const uint32_t word = s_word[p >> 5];
+        if (k0 + p < nnz && ((word >> lane) & 1u)) {
+            const int64_t pos = base + s_wpre[p >> 5] + __popc(word & ((1u << lane) - 1u));
+            if (pos < m) {
+                ocol[pos] = c[i];
+                if (osrc) osrc[pos] = (int32_t)(r0 + s_row[p]);
+            } else {
+                flag_status(ctr, ST_BADGRAPH);
             }
         }
-        carry += total;
-        __syncthreads();
     }
 }
 

@@ -352,14 +352,68 @@ __device__ __forceinline__ void tile_row_range(const int32_t *trow, const int64_
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
     if (trow) {
         r0 = trow[blockIdx.x];
-        r1 = k0 + TILE < len ? (int64_t)trow[blockIdx.x + 1] : n - 1;
         r0 = r0 < 0 ? 0 : (r0 > n - 1 ? n - 1 : r0);      // in range even for a bad CSR
+        // the last tile ends at the row of the last entry, not at the trailing empty rows
+        r1 = k0 + TILE < len ? (int64_t)trow[blockIdx.x + 1] : row_search(off, r0, n - 1, len - 1);
         r1 = r1 < r0 ? r0 : (r1 > n - 1 ? n - 1 : r1);
     } else {
         const int64_t klast = (k0 + TILE < len ? k0 + TILE : len) - 1;
         r0 = row_search(off, 0, n - 1, k0);
         r1 = row_search(off, r0, n - 1, klast);
     }
+}
+
+constexpr int64_t ROW_MARK_CAP = 4 * TILE;
+
+// Row of every entry of tile blockIdx.x, into shared memory: s_row[p] =
+// row(k0 + p) - r0 for p < TILE, where row(k) is the last nonempty row whose
+// first entry is at or before k and r0 = row(k0) (tile_row_range).  Each
+// nonempty row of [r0 + 1, r1] marks its first entry, then a block-wide
+// running maximum spreads the marks (marks grow with position), so the rows
+// are read once, coalesced, instead of one binary search per entry (kept for
+// tiles spanning more than ROW_MARK_CAP rows, i.e. long runs of empty rows).  Every
+// write stays in s_row whatever off holds, and every result lies in
+// [0, r1 - r0].  Needs blockDim.x == TILE_THREADS, s_row 16-byte aligned,
+// s_warp of TILE_THREADS / 32 ints; ends with __syncthreads().
+__device__ __forceinline__ void tile_entry_rows(const int64_t *__restrict__ off, int64_t len, int64_t r0, int64_t r1,
+                                                int32_t *s_row, int32_t *s_warp) {
+    const int64_t k0 = (int64_t)blockIdx.x * TILE;
+    const int64_t k1 = k0 + TILE < len ? k0 + TILE : len;
+    if (r1 - r0 > ROW_MARK_CAP) {          // a long run of empty rows: search per entry
+        for (int p = threadIdx.x; p < TILE; p += TILE_THREADS)
+            s_row[p] = k0 + p < k1 ? (int32_t)(row_search(off, r0, r1, k0 + p) - r0) : 0;
+        __syncthreads();
+        return;
+    }
+    for (int p = threadIdx.x; p < TILE; p += TILE_THREADS) s_row[p] = 0;
+    __syncthreads();
+    for (int64_t r = r0 + 1 + threadIdx.x; r <= r1; r += TILE_THREADS) {
+        const int64_t a = off[r];
+        if (a >= k0 && a < k1 && a < off[r + 1]) s_row[a - k0] = (int32_t)(r - r0);
+    }
+    __syncthreads();
+    static_assert(TILE_ITEMS == 8, "two int4 per thread");
+    int4 *s4 = reinterpret_cast<int4 *>(s_row) + 2 * threadIdx.x;
+    int4 a = s4[0], b = s4[1];
+    a.y = max(a.y, a.x); a.z = max(a.z, a.y); a.w = max(a.w, a.z);
+    b.x = max(b.x, a.w); b.y = max(b.y, b.x); b.z = max(b.z, b.y); b.w = max(b.w, b.z);
+    const unsigned lane = threadIdx.x & 31u;
+    int32_t inc = b.w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int32_t x = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= (unsigned)d) inc = max(inc, x);
+    }
+    int32_t pre = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) pre = 0;
+    if (lane == 31) s_warp[threadIdx.x >> 5] = inc;
+    __syncthreads();
+    for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) pre = max(pre, s_warp[w]);
+    a.x = max(a.x, pre); a.y = max(a.y, pre); a.z = max(a.z, pre); a.w = max(a.w, pre);
+    b.x = max(b.x, pre); b.y = max(b.y, pre); b.z = max(b.z, pre); b.w = max(b.w, pre);
+    s4[0] = a;
+    s4[1] = b;
+    __syncthreads();
 }
 
 // Source row of oriented edge j: from the per-edge source table osrc when

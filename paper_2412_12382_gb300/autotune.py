@@ -59,6 +59,10 @@ TUNABLES = {
     "T_BATCH": ("support.cu", [1, 2, 4, 8, 16]),          # candidates per batch of a tiled visit
     "HEAVY_CAND": ("support.cu", [4, 8, 16, 32, 64]),     # candidates per range for a centre to be tiled
     "CORE_ORDER": ("support.cu", [0, 1, 2]),                  # core visits: id order, d+ down, d+ up
+    "ORIENT_FLAGS_PERSISTENT": ("orient.cu", [0, 1]),       # orientation passes: one block per tile or
+    "ORIENT_FILL_PERSISTENT": ("orient.cu", [0, 1]),        # persistent with bulk-copied tiles
+    "ORIENT_FLAGS_MIN_BLOCKS": ("orient.cu", [1, 6, 7, 8]),  # register budget of the flag pass
+    "ORIENT_GATHER_CG": ("orient.cu", [0, 1]),              # degree gathers bypass L1
 }
 
 

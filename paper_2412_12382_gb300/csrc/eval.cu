@@ -42,6 +42,16 @@ __device__ __forceinline__ int seg_of(const int64_t *seg_off, int nseg, int64_t 
     return lo;
 }
 
+// floor(128 t / s) clamped to the last bin: a float quotient (error far
+// below 1) corrected by exact integer comparisons.
+__device__ __forceinline__ int weight_bin(uint32_t tt, int64_t s) {
+    const int64_t num = 128 * (int64_t)tt;
+    int64_t b = (int64_t)((float)num / (float)s);
+    if (b * s > num) --b;
+    else if ((b + 1) * s <= num) ++b;
+    return b > NBINS - 1 ? NBINS - 1 : (int)b;
+}
+
 __global__ void __launch_bounds__(TILE_THREADS)
 k_feat_hist(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t, int64_t n, int64_t m,
             const int32_t *orows, const int32_t *osrc, const int64_t *seg_off, int nseg, unsigned int *hist,
@@ -62,14 +72,7 @@ k_feat_hist(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const 
         int64_t b = -1, u = 0;
         if (valid) {
             u = edge_source(osrc, ooff, r0, r1, j);
-            const int64_t s = (int64_t)deg[u] + deg[ocol[j]];
-            // b = floor(128 t / s): a float quotient (error far below 1)
-            // corrected by exact integer comparisons
-            const int64_t num = 128 * (int64_t)t[j];
-            b = (int64_t)((float)num / (float)s);
-            if (b * s > num) --b;
-            else if ((b + 1) * s <= num) ++b;
-            if (b > NBINS - 1) b = NBINS - 1;
+            b = weight_bin(t[j], (int64_t)deg[u] + deg[ocol[j]]);
         }
         // bin 0 (edges in no triangle, most of a sparse graph) is counted with
         // one shared add per warp: lane-by-lane adds to one word serialise

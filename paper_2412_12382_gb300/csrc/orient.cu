@@ -8,6 +8,7 @@
 // counts, scatter of the kept ids and of the row offsets.  Each tile learns
 // the row of its entries from one coalesced read of its rows' offsets
 // (tile_entry_rows).
+#include "bulk.cuh"
 #include "tec_internal.cuh"
 
 namespace tec {
@@ -56,7 +57,7 @@ k_validate_entries(const int64_t *off, const int32_t *col, int64_t n, int64_t nn
     const int64_t k0 = (int64_t)blockIdx.x * TILE;
     int64_t r0, r1;
     tile_row_range(trow, off, n, nnz, r0, r1);
-    tile_entry_rows(off, nnz, r0, r1, s_row, s_warp);
+    tile_entry_rows(off, nnz, (int64_t)blockIdx.x, r0, r1, s_row, s_warp);
     for (int i = 0; i < TILE_ITEMS; ++i) {
         int64_t k = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
         if (k >= nnz) break;
@@ -87,83 +88,80 @@ __device__ __forceinline__ int block_sum_int(int x) {
     return tot;
 }
 
-// Pass 1: keep bit per symmetric entry (bit k of flags) and kept count per
-// tile.  The column ids of all eight items are loaded before the row pass
-// and every degree gather is issued before any is used, so each thread keeps
-// several loads in flight.
-__global__ void __launch_bounds__(TILE_THREADS)
-k_orient_flags(const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ deg,
-               int64_t n, int64_t nnz, const int32_t *__restrict__ trow, uint32_t *__restrict__ flags,
-               int64_t *__restrict__ tile_cnt, unsigned long long *ctr) {
-    __shared__ __align__(16) int32_t s_row[TILE];
-    __shared__ int32_t s_warp[TILE_THREADS / 32];
-    const int64_t k0 = (int64_t)blockIdx.x * TILE;
-    int64_t r0, r1;
-    tile_row_range(trow, off, n, nnz, r0, r1);
-    int32_t v[TILE_ITEMS];
-#pragma unroll
-    for (int i = 0; i < TILE_ITEMS; ++i) {
-        const int64_t k = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
-        v[i] = k < nnz ? col[k] : 0;
-    }
-    tile_entry_rows(off, nnz, r0, r1, s_row, s_warp);
-    int32_t du[TILE_ITEMS], dv[TILE_ITEMS];
+// Whether each orientation pass runs as the persistent bulk-copy kernel (1)
+// or as one block per tile reading global memory (0), the blocks per SM the
+// one-block-per-tile flag pass is compiled for (register budget), and whether
+// its degree gathers bypass L1; chosen by the autotuner.
+constexpr int ORIENT_FLAGS_PERSISTENT = 0;
+constexpr int ORIENT_FILL_PERSISTENT = 0;
+constexpr int ORIENT_FLAGS_MIN_BLOCKS = 1;
+constexpr int ORIENT_GATHER_CG = 1;
+
+// Pass 1 on one tile of `cnt` symmetric entries whose column ids are read
+// from sc (shared or global memory): keep bit per entry (bit k of flags) and
+// the tile's kept count.  The degree gathers of the eight items' columns are
+// issued first and stay in flight while the tile's rows are worked out.
+__device__ __forceinline__ void flags_tile(const int32_t *sc, int64_t tile, int cnt, const int64_t *__restrict__ off,
+                                           const int32_t *__restrict__ deg, int64_t n, int64_t nnz,
+                                           const int32_t *__restrict__ trow, uint32_t *__restrict__ flags,
+                                           int64_t *__restrict__ tile_cnt, int32_t *s_row, int32_t *s_warp,
+                                           unsigned long long *ctr) {
+    int32_t v[TILE_ITEMS], dv[TILE_ITEMS];
     bool bad = false;
 #pragma unroll
     for (int i = 0; i < TILE_ITEMS; ++i) {
-        const int64_t k = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
-        const bool in = k < nnz && v[i] >= 0 && (int64_t)v[i] < n;
-        bad |= k < nnz && !in;
-        du[i] = in ? deg[r0 + s_row[i * TILE_THREADS + threadIdx.x]] : 0;
-        dv[i] = in ? deg[v[i]] : 0;
+        const int x = i * TILE_THREADS + (int)threadIdx.x;
+        v[i] = x < cnt ? sc[x] : -1;
+        const bool in = v[i] >= 0 && (int64_t)v[i] < n;
+        bad |= x < cnt && !in;
+        if (!in) v[i] = -1;
+        dv[i] = in ? (ORIENT_GATHER_CG ? __ldcg(&deg[v[i]]) : deg[v[i]]) : 0;
     }
     if (bad) flag_status(ctr, ST_BADGRAPH);
-    int cnt = 0;
+    int64_t r0, r1;
+    tile_row_range(trow, off, n, nnz, tile, r0, r1);
+    tile_entry_rows(off, nnz, tile, r0, r1, s_row, s_warp);
+    const unsigned lane = lane_id();
+    int c = 0;
 #pragma unroll
     for (int i = 0; i < TILE_ITEMS; ++i) {
-        const int64_t kw = k0 + (int64_t)i * TILE_THREADS + (threadIdx.x & ~31u);
-        const int64_t k = kw + lane_id();
-        const int64_t u = r0 + s_row[i * TILE_THREADS + threadIdx.x];
-        const bool f = k < nnz && v[i] >= 0 && (int64_t)v[i] < n && rank_less(du[i], u, dv[i], v[i]);
+        const int x = i * TILE_THREADS + (int)threadIdx.x;
+        const int xw = x - (int)lane;
+        const int64_t u = r0 + s_row[x];
+        const bool f = v[i] >= 0 && rank_less(deg[u], u, dv[i], v[i]);
         const unsigned b = __ballot_sync(0xffffffffu, f);
-        if (lane_id() == 0 && kw < nnz) flags[kw >> 5] = b;
-        cnt += f ? 1 : 0;
+        if (lane == 0 && xw < cnt) flags[(tile * TILE + xw) >> 5] = b;
+        c += f ? 1 : 0;
     }
-    int tot = block_sum_int(cnt);
-    if (threadIdx.x == 0) tile_cnt[blockIdx.x] = tot;
+    const int tot = block_sum_int(c);
+    if (threadIdx.x == 0) tile_cnt[tile] = tot;
 }
 
-// Pass 2: scatter kept ids to ocol[global rank of the keep bit] (and the
-// source row to osrc) and write ooff[u] for every row that starts (or, if
-// empty, sits) at an entry of this tile.  The rank of a keep bit is the
-// tile's base plus a popcount prefix of the tile's 64 flag words, kept in
-// shared memory; there is no per-item barrier.
-__global__ void __launch_bounds__(TILE_THREADS)
-k_orient_fill(const int64_t *__restrict__ off, const int32_t *__restrict__ col, int64_t n, int64_t nnz,
-              const int32_t *__restrict__ trow, const uint32_t *__restrict__ flags,
-              const int64_t *__restrict__ tile_base, int64_t *__restrict__ ooff, int32_t *__restrict__ ocol,
-              int32_t *__restrict__ osrc, int64_t m, unsigned long long *ctr) {
+// Pass 2 on one tile of `cnt` entries, column ids from sc and its flag words
+// from sw (shared or global memory): scatter of the kept ids to
+// ocol[global rank of the keep bit] (and of the source row to osrc), and
+// ooff[u] for every row that starts (or, if empty, sits) at an entry of the
+// tile.  The rank of a keep bit is the tile's base plus a popcount prefix of
+// the tile's flag words.
+__device__ __forceinline__ void fill_tile(const int32_t *sc, const uint32_t *sw, int64_t tile, int cnt,
+                                          const int64_t *__restrict__ off, int64_t n, int64_t nnz,
+                                          const int32_t *__restrict__ trow, const int64_t *__restrict__ tile_base,
+                                          int64_t *__restrict__ ooff, int32_t *__restrict__ ocol,
+                                          int32_t *__restrict__ osrc, int64_t m, int32_t *s_row, int32_t *s_warp,
+                                          int32_t *s_wpre, uint32_t *s_word, unsigned long long *ctr) {
     constexpr int WORDS = TILE / 32;
-    __shared__ __align__(16) int32_t s_row[TILE];
-    __shared__ int32_t s_warp[TILE_THREADS / 32];
-    __shared__ uint32_t s_word[WORDS];
-    __shared__ int32_t s_wpre[WORDS];
-    const int64_t k0 = (int64_t)blockIdx.x * TILE;
+    static_assert(WORDS == 64, "two flag words per lane of warp 0");
     int64_t r0, r1;
-    tile_row_range(trow, off, n, nnz, r0, r1);
-    const int64_t base = tile_base[blockIdx.x];
+    tile_row_range(trow, off, n, nnz, tile, r0, r1);
+    const int64_t base = tile_base[tile];
     int32_t c[TILE_ITEMS];
 #pragma unroll
     for (int i = 0; i < TILE_ITEMS; ++i) {
-        const int64_t k = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
-        c[i] = k < nnz ? col[k] : 0;
+        const int x = i * TILE_THREADS + (int)threadIdx.x;
+        c[i] = x < cnt ? sc[x] : 0;
     }
-    if (threadIdx.x < WORDS) {
-        const int64_t kw = k0 + (int64_t)threadIdx.x * 32;
-        s_word[threadIdx.x] = kw < nnz ? flags[kw >> 5] : 0u;
-    }
-    tile_entry_rows(off, nnz, r0, r1, s_row, s_warp);    // its barriers publish s_word
-    static_assert(WORDS == 64, "two flag words per lane of warp 0");
+    if (threadIdx.x < WORDS) s_word[threadIdx.x] = 32 * (int)threadIdx.x < cnt ? sw[threadIdx.x] : 0u;
+    tile_entry_rows(off, nnz, tile, r0, r1, s_row, s_warp);    // its barriers publish s_word
     if (threadIdx.x < 32) {
         const int a = __popc(s_word[2 * threadIdx.x]), b = __popc(s_word[2 * threadIdx.x + 1]);
         int inc = a + b;
@@ -176,7 +174,7 @@ k_orient_fill(const int64_t *__restrict__ off, const int32_t *__restrict__ col, 
         s_wpre[2 * threadIdx.x + 1] = inc - b;
     }
     __syncthreads();
-    const int64_t k1 = k0 + TILE < nnz ? k0 + TILE : nnz;
+    const int64_t k0 = tile * TILE, k1 = k0 + cnt;
     // oriented offsets of the rows whose first entry lies in the tile
     for (int64_t r = r0 + threadIdx.x; r <= r1; r += TILE_THREADS) {
         const int64_t a = off[r];
@@ -193,7 +191,7 @@ k_orient_fill(const int64_t *__restrict__ off, const int32_t *__restrict__ col, 
     for (int i = 0; i < TILE_ITEMS; ++i) {
         const int p = i * TILE_THREADS + (int)threadIdx.x;
         const uint32_t word = s_word[p >> 5];
-        if (k0 + p < nnz && ((word >> lane) & 1u)) {
+        if (p < cnt && ((word >> lane) & 1u)) {
             const int64_t pos = base + s_wpre[p >> 5] + __popc(word & ((1u << lane) - 1u));
             if (pos < m) {
                 ocol[pos] = c[i];
@@ -202,6 +200,68 @@ k_orient_fill(const int64_t *__restrict__ off, const int32_t *__restrict__ col, 
                 flag_status(ctr, ST_BADGRAPH);
             }
         }
+    }
+}
+
+constexpr uint32_t OB_COL_BYTES = TILE * 4;
+constexpr uint32_t OB_WORD_BYTES = TILE / 8;
+
+// Both passes run as persistent kernels: each block walks tiles blockIdx.x,
+// + gridDim.x, ..., and while it works on one tile the copy engine brings the
+// column ids (and, in pass 2, the flag words) of its next tile into the other
+// shared-memory stage.  A partial last tile is read from global memory.  A
+// copy that does not land within the wait cap sets ST_TIMEOUT.
+template <bool FILL, bool BULK>
+__global__ void __launch_bounds__(TILE_THREADS, (BULK || FILL) ? 1 : ORIENT_FLAGS_MIN_BLOCKS)
+k_orient_pass(const int64_t *__restrict__ off, const int32_t *__restrict__ col, const int32_t *__restrict__ deg,
+              int64_t n, int64_t nnz, const int32_t *__restrict__ trow,
+              uint32_t *__restrict__ flags, int64_t *__restrict__ tile_cnt, const int64_t *__restrict__ tile_base,
+              int64_t *__restrict__ ooff, int32_t *__restrict__ ocol, int32_t *__restrict__ osrc, int64_t m,
+              unsigned long long *ctr) {
+    __shared__ __align__(16) int32_t s_col[BULK_STAGES * TILE];
+    __shared__ __align__(16) uint32_t s_w[FILL ? BULK_STAGES * (TILE / 32) : 4];
+    __shared__ __align__(16) int32_t s_row[TILE];
+    __shared__ int32_t s_warp[TILE_THREADS / 32];
+    __shared__ int32_t s_wpre[TILE / 32];
+    __shared__ uint32_t s_word[TILE / 32];
+    __shared__ uint64_t bar[BULK_STAGES];
+    __shared__ int s_flag;
+    if (!BULK) {                                 // one tile per block, read from global memory
+        const int64_t tile = blockIdx.x;
+        const int cnt = (int)(nnz - tile * TILE < TILE ? nnz - tile * TILE : TILE);
+        if (FILL)
+            fill_tile(col + tile * TILE, flags + tile * (TILE / 32), tile, cnt, off, n, nnz, trow, tile_base, ooff,
+                      ocol, osrc, m, s_row, s_warp, s_wpre, s_word, ctr);
+        else
+            flags_tile(col + tile * TILE, tile, cnt, off, deg, n, nnz, trow, flags, tile_cnt, s_row, s_warp, ctr);
+        return;
+    }
+    const int64_t full = nnz / TILE;
+    bulk_init(bar, &s_flag);
+    const bool ok = bulk_tiles(
+        full, bar, &s_flag, ctr,
+        [&](int64_t tile, int stage) {
+            fence_proxy_async();
+            mbar_arrive_expect_tx(&bar[stage], OB_COL_BYTES + (FILL ? OB_WORD_BYTES : 0u));
+            bulk_g2s(s_col + stage * TILE, col + tile * TILE, OB_COL_BYTES, &bar[stage]);
+            if (FILL) bulk_g2s(s_w + stage * (TILE / 32), flags + tile * (TILE / 32), OB_WORD_BYTES, &bar[stage]);
+        },
+        [&](int64_t tile, int stage) {
+            if (FILL)
+                fill_tile(s_col + stage * TILE, s_w + stage * (TILE / 32), tile, TILE, off, n, nnz, trow, tile_base,
+                          ooff, ocol, osrc, m, s_row, s_warp, s_wpre, s_word, ctr);
+            else
+                flags_tile(s_col + stage * TILE, tile, TILE, off, deg, n, nnz, trow, flags, tile_cnt, s_row, s_warp,
+                           ctr);
+        });
+    if (!ok) return;
+    if (full * TILE < nnz && blockIdx.x == (unsigned)(full % gridDim.x)) {
+        const int cnt = (int)(nnz - full * TILE);
+        if (FILL)
+            fill_tile(col + full * TILE, flags + full * (TILE / 32), full, cnt, off, n, nnz, trow, tile_base, ooff,
+                      ocol, osrc, m, s_row, s_warp, s_wpre, s_word, ctr);
+        else
+            flags_tile(col + full * TILE, full, cnt, off, deg, n, nnz, trow, flags, tile_cnt, s_row, s_warp, ctr);
     }
 }
 
@@ -273,19 +333,39 @@ cudaError_t launch_validate_entries(const int64_t *off, const int32_t *col, int6
     return cudaGetLastError();
 }
 
+
+template <bool FILL>
+cudaError_t launch_orient_pass(const int64_t *off, const int32_t *col, const int32_t *deg, int64_t n, int64_t nnz,
+                               const int32_t *trow, uint32_t *flags, int64_t *tile_cnt, const int64_t *tile_base,
+                               int64_t *ooff, int32_t *ocol, int32_t *osrc, int64_t m, unsigned long long *ctr,
+                               cudaStream_t s) {
+    constexpr bool BULK = FILL ? ORIENT_FILL_PERSISTENT != 0 : ORIENT_FLAGS_PERSISTENT != 0;
+    unsigned grid = (unsigned)ceil_div(nnz, TILE);
+    if (BULK) {
+        cudaError_t e = persistent_grid(k_orient_pass<FILL, BULK>, TILE_THREADS, 0, nnz / TILE, &grid);
+        if (e != cudaSuccess) return e;
+    }
+    k_orient_pass<FILL, BULK><<<grid, TILE_THREADS, 0, s>>>(off, col, deg, n, nnz, trow, flags, tile_cnt, tile_base,
+                                                            ooff, ocol, osrc, m, ctr);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_orient(const int64_t *off, const int32_t *col, const int32_t *deg, int64_t n,
                           int64_t nnz, const int32_t *trow, uint32_t *flags, int64_t *tile_cnt, int64_t *tile_base,
                           int64_t *bsum, int64_t *ooff, int32_t *ocol, int32_t *osrc, int64_t m,
                           unsigned long long *ctr, cudaStream_t s) {
     const int64_t ntiles = ceil_div(nnz, TILE);
+    if (((uintptr_t)col | (uintptr_t)flags) % 16 != 0) return cudaErrorInvalidValue;
     if (ntiles > 0) {
-        k_orient_flags<<<(unsigned)ntiles, TILE_THREADS, 0, s>>>(off, col, deg, n, nnz, trow, flags, tile_cnt, ctr);
-    count_launches(1);
-        cudaError_t e = scan_exclusive_i64(tile_cnt, ntiles, tile_base, bsum, s);
+        cudaError_t e = launch_orient_pass<false>(off, col, deg, n, nnz, trow, flags, tile_cnt, tile_base, ooff,
+                                                  ocol, osrc, m, ctr, s);
         if (e != cudaSuccess) return e;
-        k_orient_fill<<<(unsigned)ntiles, TILE_THREADS, 0, s>>>(off, col, n, nnz, trow, flags, tile_base, ooff,
-                                                               ocol, osrc, m, ctr);
-        count_launches(1);
+        e = scan_exclusive_i64(tile_cnt, ntiles, tile_base, bsum, s);
+        if (e != cudaSuccess) return e;
+        e = launch_orient_pass<true>(off, col, deg, n, nnz, trow, flags, tile_cnt, tile_base, ooff, ocol, osrc,
+                                     m, ctr, s);
+        if (e != cudaSuccess) return e;
     } else {
         cudaError_t e = scan_exclusive_i64(tile_cnt, 0, tile_base, bsum, s);
         if (e != cudaSuccess) return e;

@@ -52,16 +52,17 @@ k_prune(const int64_t *__restrict__ ooff, const int32_t *__restrict__ ocol, cons
         v[i] = in ? ocol[j] : 0;
         tt[i] = in ? t[j] : 0u;
     }
-    int32_t sd[TILE_ITEMS];                    // deg u, then deg u + deg v
+    uint32_t sd[TILE_ITEMS];                   // deg u, then deg u + deg v (< 2^32)
 #pragma unroll
-    for (int i = 0; i < TILE_ITEMS; ++i) sd[i] = k0 + (int64_t)i * TILE_THREADS + threadIdx.x < m ? deg[u[i]] : 0;
+    for (int i = 0; i < TILE_ITEMS; ++i)
+        sd[i] = k0 + (int64_t)i * TILE_THREADS + threadIdx.x < m ? (uint32_t)deg[u[i]] : 0u;
     unsigned pre = 0;                          // bit i: item i passes at s = 2 deg u
 #pragma unroll
     for (int i = 0; i < TILE_ITEMS; ++i) {
         const int64_t j = k0 + (int64_t)i * TILE_THREADS + threadIdx.x;
         if (j < m && keep_edge<WIDE>(measure, tt[i], 2 * (int64_t)sd[i], p, q)) {
             pre |= 1u << i;
-            sd[i] += deg[v[i]];
+            sd[i] += (uint32_t)deg[v[i]];
         }
     }
     int kept = 0;
@@ -103,15 +104,15 @@ __device__ __forceinline__ int prune_tile(const int32_t *su, const int32_t *sv, 
         v[i] = in ? sv[x] : 0;
         tt[i] = in ? st[x] : 0u;
     }
-    int32_t sd[TILE_ITEMS];
+    uint32_t sd[TILE_ITEMS];                   // deg u, then deg u + deg v (< 2^32)
 #pragma unroll
-    for (int i = 0; i < TILE_ITEMS; ++i) sd[i] = i * TILE_THREADS + (int)threadIdx.x < cnt ? deg[u[i]] : 0;
+    for (int i = 0; i < TILE_ITEMS; ++i) sd[i] = i * TILE_THREADS + (int)threadIdx.x < cnt ? (uint32_t)deg[u[i]] : 0u;
     unsigned pre = 0;
 #pragma unroll
     for (int i = 0; i < TILE_ITEMS; ++i) {
         if (i * TILE_THREADS + (int)threadIdx.x < cnt && keep_edge<WIDE>(measure, tt[i], 2 * (int64_t)sd[i], p, q)) {
             pre |= 1u << i;
-            sd[i] += deg[v[i]];
+            sd[i] += (uint32_t)deg[v[i]];
         }
     }
     const unsigned lane = lane_id();
@@ -128,9 +129,8 @@ __device__ __forceinline__ int prune_tile(const int32_t *su, const int32_t *sv, 
     return kept;
 }
 
-constexpr int PB_STAGES = 2;
 constexpr uint32_t PB_ARRAY_BYTES = TILE * 4;                  // one array's share of a tile
-constexpr size_t PB_SMEM = (size_t)PB_STAGES * 3 * PB_ARRAY_BYTES;
+constexpr size_t PB_SMEM = (size_t)BULK_STAGES * 3 * PB_ARRAY_BYTES;
 
 // k_prune for graphs with a per-edge source table, as a persistent kernel:
 // each block walks tiles blockIdx.x, + gridDim.x, ..., and while it tests one
@@ -145,58 +145,30 @@ k_prune_bulk(const int32_t *__restrict__ ocol, const int32_t *__restrict__ deg, 
              uint32_t *__restrict__ keep, int32_t *parent, unsigned long long *ctr) {
     extern __shared__ __align__(16) unsigned char pb_smem[];
     int32_t *buf = reinterpret_cast<int32_t *>(pb_smem);
-    __shared__ uint64_t bar[PB_STAGES];
+    __shared__ uint64_t bar[BULK_STAGES];
     __shared__ int ws[TILE_THREADS / 32];
     __shared__ int s_flag;
     const int64_t full = m / TILE;
-    if (threadIdx.x == 0) {
-        for (int x = 0; x < PB_STAGES; ++x) mbar_init(&bar[x], 1);
-        fence_mbar_init();
-        s_flag = graph_bad(ctr) ? 1 : 0;
-    }
-    __syncthreads();
-    if (s_flag) return;
-    auto issue = [&](int64_t tile, int stage) {
-        int32_t *dst = buf + (size_t)stage * 3 * TILE;
-        const int64_t j0 = tile * TILE;
-        fence_proxy_async();
-        mbar_arrive_expect_tx(&bar[stage], 3 * PB_ARRAY_BYTES);
-        bulk_g2s(dst, osrc + j0, PB_ARRAY_BYTES, &bar[stage]);
-        bulk_g2s(dst + TILE, ocol + j0, PB_ARRAY_BYTES, &bar[stage]);
-        bulk_g2s(dst + 2 * TILE, t + j0, PB_ARRAY_BYTES, &bar[stage]);
-    };
-    int64_t tile = blockIdx.x;
-    if (threadIdx.x == 0 && tile < full) issue(tile, 0);
-    uint32_t phase = 0;                      // bit x: parity of stage x's next phase
-    uint32_t pending = tile < full ? 1u : 0u;  // bit x: a copy into stage x not yet waited for
+    bulk_init(bar, &s_flag);
+    if (graph_bad(ctr)) return;              // uniform: nothing in this launch sets the bit
     int kept = 0;
-    for (int it = 0; tile < full; ++it, tile += gridDim.x) {
-        const int stage = it & 1;
-        const int64_t nxt = tile + gridDim.x;
-        if (nxt < full) {
-            if (threadIdx.x == 0) issue(nxt, stage ^ 1);
-            pending |= 1u << (stage ^ 1);
-        }
-        if (!mbar_wait(&bar[stage], (phase >> stage) & 1u)) s_flag = 1;
-        phase ^= 1u << stage;
-        pending &= ~(1u << stage);
-        __syncthreads();
-        if (s_flag) break;
-        const int32_t *su = buf + (size_t)stage * 3 * TILE;
-        kept += prune_tile<HOOK, WIDE>(su, su + TILE, reinterpret_cast<const uint32_t *>(su + 2 * TILE), tile * TILE,
-                                       TILE, deg, measure, p, q, keep, parent, ctr);
-        fence_proxy_async();                 // the stage is read before the copy engine refills it
-        __syncthreads();
-    }
-    if (s_flag) {
-        // let the copies still in flight land (bounded) before the block exits
-        if (threadIdx.x == 0) {
-            flag_status(ctr, ST_TIMEOUT);
-            for (int x = 0; x < PB_STAGES; ++x)
-                if ((pending >> x) & 1u) mbar_wait(&bar[x], (phase >> x) & 1u);
-        }
-        return;
-    }
+    const bool ok = bulk_tiles(
+        full, bar, &s_flag, ctr,
+        [&](int64_t tile, int stage) {
+            int32_t *dst = buf + (size_t)stage * 3 * TILE;
+            const int64_t j0 = tile * TILE;
+            fence_proxy_async();
+            mbar_arrive_expect_tx(&bar[stage], 3 * PB_ARRAY_BYTES);
+            bulk_g2s(dst, osrc + j0, PB_ARRAY_BYTES, &bar[stage]);
+            bulk_g2s(dst + TILE, ocol + j0, PB_ARRAY_BYTES, &bar[stage]);
+            bulk_g2s(dst + 2 * TILE, t + j0, PB_ARRAY_BYTES, &bar[stage]);
+        },
+        [&](int64_t tile, int stage) {
+            const int32_t *su = buf + (size_t)stage * 3 * TILE;
+            kept += prune_tile<HOOK, WIDE>(su, su + TILE, reinterpret_cast<const uint32_t *>(su + 2 * TILE),
+                                           tile * TILE, TILE, deg, measure, p, q, keep, parent, ctr);
+        });
+    if (!ok) return;
     if (full * TILE < m && blockIdx.x == (unsigned)(full % gridDim.x)) {
         const int64_t j0 = full * TILE;
         kept += prune_tile<HOOK, WIDE>(osrc + j0, ocol + j0, t + j0, j0, (int)(m - j0), deg, measure, p, q, keep,
@@ -345,18 +317,11 @@ template <bool HOOK, bool WIDE>
 cudaError_t launch_bulk(const int32_t *ocol, const int32_t *deg, const uint32_t *t, int64_t m, const int32_t *osrc,
                         const PruneArgs &a, uint32_t *keep, int32_t *parent, unsigned long long *ctr,
                         cudaStream_t s) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_prune_bulk<HOOK, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB_SMEM);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prune_bulk<HOOK, WIDE>, TILE_THREADS, PB_SMEM);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_prune_bulk<HOOK, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PB_SMEM);
+    unsigned grid = 1;
+    if (e == cudaSuccess) e = persistent_grid(k_prune_bulk<HOOK, WIDE>, TILE_THREADS, PB_SMEM, m / TILE, &grid);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    const int64_t full = m / TILE;
-    const int64_t want = (int64_t)sms * per_sm;
-    const unsigned grid = (unsigned)(want < full ? want : full);
     k_prune_bulk<HOOK, WIDE><<<grid, TILE_THREADS, PB_SMEM, s>>>(ocol, deg, t, m, osrc, a.measure, a.p, a.q, keep,
                                                                  parent, ctr);
     count_launches(1);

@@ -100,6 +100,7 @@ cudaError_t launch_validate(const int64_t *off, const int32_t *col, int64_t n, i
 cudaError_t launch_validate_entries(const int64_t *off, const int32_t *col, int64_t n, int64_t nnz,
                                     const int32_t *trow, unsigned long long *ctr, cudaStream_t s);
 // osrc (m entries, or nullptr) receives the source row of every oriented edge.
+// col and flags 16-byte aligned (cudaInvalidValue otherwise).
 cudaError_t launch_orient(const int64_t *off, const int32_t *col, const int32_t *deg, int64_t n,
                           int64_t nnz, const int32_t *trow, uint32_t *flags, int64_t *tile_cnt, int64_t *tile_base,
                           int64_t *bsum, int64_t *ooff, int32_t *ocol, int32_t *osrc, int64_t m,
@@ -343,18 +344,18 @@ __device__ __forceinline__ int64_t row_search(const int64_t *off, int64_t lo, in
     return lo;
 }
 
-// Rows of tile blockIdx.x (entries [blockIdx.x * TILE, + TILE) of a CSR with
-// `len` entries): r0 = the row of its first entry, r1 >= the row of its last.
+// Rows of tile `tile` (entries [tile * TILE, + TILE) of a CSR with `len`
+// entries): r0 = the row of its first entry, r1 >= the row of its last.
 // From the tile-row table trow of launch_tile_rows when given (two loads),
 // else by binary search over all n rows.
 __device__ __forceinline__ void tile_row_range(const int32_t *trow, const int64_t *off, int64_t n, int64_t len,
-                                               int64_t &r0, int64_t &r1) {
-    const int64_t k0 = (int64_t)blockIdx.x * TILE;
+                                               int64_t tile, int64_t &r0, int64_t &r1) {
+    const int64_t k0 = tile * TILE;
     if (trow) {
-        r0 = trow[blockIdx.x];
+        r0 = trow[tile];
         r0 = r0 < 0 ? 0 : (r0 > n - 1 ? n - 1 : r0);      // in range even for a bad CSR
         // the last tile ends at the row of the last entry, not at the trailing empty rows
-        r1 = k0 + TILE < len ? (int64_t)trow[blockIdx.x + 1] : row_search(off, r0, n - 1, len - 1);
+        r1 = k0 + TILE < len ? (int64_t)trow[tile + 1] : row_search(off, r0, n - 1, len - 1);
         r1 = r1 < r0 ? r0 : (r1 > n - 1 ? n - 1 : r1);
     } else {
         const int64_t klast = (k0 + TILE < len ? k0 + TILE : len) - 1;
@@ -363,9 +364,14 @@ __device__ __forceinline__ void tile_row_range(const int32_t *trow, const int64_
     }
 }
 
+__device__ __forceinline__ void tile_row_range(const int32_t *trow, const int64_t *off, int64_t n, int64_t len,
+                                               int64_t &r0, int64_t &r1) {
+    tile_row_range(trow, off, n, len, (int64_t)blockIdx.x, r0, r1);
+}
+
 constexpr int64_t ROW_MARK_CAP = 4 * TILE;
 
-// Row of every entry of tile blockIdx.x, into shared memory: s_row[p] =
+// Row of every entry of tile `tile`, into shared memory: s_row[p] =
 // row(k0 + p) - r0 for p < TILE, where row(k) is the last nonempty row whose
 // first entry is at or before k and r0 = row(k0) (tile_row_range).  Each
 // nonempty row of [r0 + 1, r1] marks its first entry, then a block-wide
@@ -375,9 +381,9 @@ constexpr int64_t ROW_MARK_CAP = 4 * TILE;
 // write stays in s_row whatever off holds, and every result lies in
 // [0, r1 - r0].  Needs blockDim.x == TILE_THREADS, s_row 16-byte aligned,
 // s_warp of TILE_THREADS / 32 ints; ends with __syncthreads().
-__device__ __forceinline__ void tile_entry_rows(const int64_t *__restrict__ off, int64_t len, int64_t r0, int64_t r1,
-                                                int32_t *s_row, int32_t *s_warp) {
-    const int64_t k0 = (int64_t)blockIdx.x * TILE;
+__device__ __forceinline__ void tile_entry_rows(const int64_t *__restrict__ off, int64_t len, int64_t tile, int64_t r0,
+                                                int64_t r1, int32_t *s_row, int32_t *s_warp) {
+    const int64_t k0 = tile * TILE;
     const int64_t k1 = k0 + TILE < len ? k0 + TILE : len;
     if (r1 - r0 > ROW_MARK_CAP) {          // a long run of empty rows: search per entry
         for (int p = threadIdx.x; p < TILE; p += TILE_THREADS)

@@ -63,6 +63,7 @@ TUNABLES = {
     "ORIENT_FILL_PERSISTENT": ("orient.cu", [0, 1]),        # persistent with bulk-copied tiles
     "ORIENT_FLAGS_MIN_BLOCKS": ("orient.cu", [1, 6, 7, 8]),  # register budget of the flag pass
     "ORIENT_GATHER_CG": ("orient.cu", [0, 1]),              # degree gathers bypass L1
+    "PRUNE_SEG_ITEMS": ("prune.cu", [1, 2, 4, 8]),          # batched prune: items whose loads fly together
 }
 
 

@@ -42,11 +42,12 @@ __device__ __forceinline__ int seg_of(const int64_t *seg_off, int nseg, int64_t 
     return lo;
 }
 
-// floor(128 t / s) clamped to the last bin: a float quotient (error far
-// below 1) corrected by exact integer comparisons.
+// floor(128 t / s) clamped to the last bin: an approximate float quotient
+// (__fdividef: a few ulp of a value below 64, so off by at most one)
+// corrected by exact integer comparisons.
 __device__ __forceinline__ int weight_bin(uint32_t tt, int64_t s) {
     const int64_t num = 128 * (int64_t)tt;
-    int64_t b = (int64_t)((float)num / (float)s);
+    int64_t b = (int64_t)__fdividef((float)num, (float)s);
     if (b * s > num) --b;
     else if ((b + 1) * s <= num) ++b;
     return b > NBINS - 1 ? NBINS - 1 : (int)b;

@@ -185,9 +185,12 @@ k_prune_bulk(const int32_t *__restrict__ ocol, const int32_t *__restrict__ deg, 
 }
 
 // Per-graph thresholds: the edge's graph is the segment of its source row.
-// One item at a time: with a third or more of the edges kept, the hooks
-// dominate and want occupancy, which batching the loads of eight items (116
-// registers) halved (measured 1.95 -> 4.2 ms on the 500-graph batch).
+// With a third or more of the edges kept the hooks dominate and want
+// occupancy: loading all eight items ahead (116 registers) took the
+// 500-graph batch from 1.95 to 4.2 ms.  Items in flight per group, chosen by
+// the autotuner:
+constexpr int PRUNE_SEG_ITEMS = 1;
+
 template <bool HOOK>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_prune_seg(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const uint32_t *t, int64_t n, int64_t m,
@@ -215,27 +218,39 @@ k_prune_seg(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const 
     }
     const unsigned lane = lane_id();
     int kept = 0;
-    for (int i = 0; i < TILE_ITEMS; ++i) {
-        const int64_t jw = k0 + (int64_t)i * TILE_THREADS + (threadIdx.x & ~31u);
-        const int64_t j = jw + lane;
-        bool kp = false;
-        if (j < m) {
-            const int64_t u = edge_source(osrc, ooff, r0, r1, j);
-            int lo = s0, hi = s1;                    // segment of u
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (seg_off[mid] <= u) lo = mid; else hi = mid - 1;
+    // PRUNE_SEG_ITEMS items at a time: their loads are issued together, then
+    // their kept edges are hooked
+    static_assert(TILE_ITEMS % PRUNE_SEG_ITEMS == 0, "whole groups of items");
+    for (int i0 = 0; i0 < TILE_ITEMS; i0 += PRUNE_SEG_ITEMS) {
+        int32_t u[PRUNE_SEG_ITEMS], v[PRUNE_SEG_ITEMS];
+        bool kp[PRUNE_SEG_ITEMS];
+#pragma unroll
+        for (int b = 0; b < PRUNE_SEG_ITEMS; ++b) {
+            const int64_t j = k0 + (int64_t)(i0 + b) * TILE_THREADS + threadIdx.x;
+            kp[b] = false;
+            u[b] = v[b] = 0;
+            if (j < m) {
+                u[b] = (int32_t)edge_source(osrc, ooff, r0, r1, j);
+                int lo = s0, hi = s1;                // segment of u
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (seg_off[mid] <= u[b]) lo = mid; else hi = mid - 1;
+                }
+                v[b] = ocol[j];
+                const int64_t s = (int64_t)deg[u[b]] + deg[v[b]];
+                const int64_t p = sp[lo], q = sq[lo];
+                kp[b] = q > 0 && (needs_wide_dev(p, q) ? keep_edge<true>(measure, t[j], s, p, q)
+                                                       : keep_edge<false>(measure, t[j], s, p, q));
             }
-            const int32_t v = ocol[j];
-            const int64_t s = (int64_t)deg[u] + deg[v];
-            const int64_t p = sp[lo], q = sq[lo];
-            kp = q > 0 && (needs_wide_dev(p, q) ? keep_edge<true>(measure, t[j], s, p, q)
-                                                : keep_edge<false>(measure, t[j], s, p, q));
-            if (HOOK && kp) uf_link(parent, (int32_t)u, v, ctr);
         }
-        const unsigned b = __ballot_sync(0xffffffffu, kp);
-        if (lane == 0 && jw < m) keep[jw >> 5] = b;
-        kept += kp ? 1 : 0;
+#pragma unroll
+        for (int b = 0; b < PRUNE_SEG_ITEMS; ++b) {
+            const int64_t jw = k0 + (int64_t)(i0 + b) * TILE_THREADS + (threadIdx.x & ~31u);
+            if (HOOK && kp[b]) uf_link(parent, u[b], v[b], ctr);
+            const unsigned w = __ballot_sync(0xffffffffu, kp[b]);
+            if (lane == 0 && jw < m) keep[jw >> 5] = w;
+            kept += kp[b] ? 1 : 0;
+        }
     }
     kept = warp_sum(kept);
     if (lane == 0) ws[threadIdx.x >> 5] = kept;

@@ -138,8 +138,8 @@ k_msf_offer_list(int32_t *lu, int32_t *lv, unsigned long long *lk, int32_t *rcnt
             ru[i] = rv[i] = 0;
             key[i] = 0;
             if (idx >= cnt) continue;
-            const int32_t a = uf_find(parent, lu[base + idx]);
-            const int32_t b = uf_find(parent, lv[base + idx]);
+            int32_t a, b;
+            uf_find2(parent, lu[base + idx], lv[base + idx], a, b);
             if (a == b) continue;
             key[i] = lk[base + idx];
             ru[i] = a;
@@ -185,7 +185,8 @@ k_msf_offer(const int64_t *ooff, const int32_t *ocol, const uint8_t *lvl, int64_
             const uint8_t L = lvl[j] & (uint8_t)~FOREST_BIT;
             if (L == 0) continue;
             const int32_t u = (int32_t)edge_source(osrc, ooff, r0, r1, j);
-            const int32_t ru = uf_find(parent, u), rv = uf_find(parent, ocol[j]);
+            int32_t ru, rv;
+            uf_find2(parent, u, ocol[j], ru, rv);
             if (ru == rv) continue;
             const uint64_t key = msf_key(L, j);
             atomicMax(&best[ru], (unsigned long long)key);

@@ -28,6 +28,40 @@ __device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x) {
     return uf_find_from(parent, x, __ldcg(&parent[x]));
 }
 
+// The roots of a and b, walked side by side: each step issues the loads of
+// both walks before using either, so a link waits for the longer of the two
+// pointer chains rather than their sum.  Each walk is uf_find's (same path
+// halving writes, same result).
+__device__ __forceinline__ void uf_find2(int32_t *parent, int32_t a, int32_t b, int32_t &ra, int32_t &rb) {
+    int32_t pa = a, ca = __ldcg(&parent[a]);
+    int32_t pb = b, cb = __ldcg(&parent[b]);
+    bool wa = ca != a, wb = cb != b;             // still walking
+    while (wa || wb) {
+        const int32_t na = wa ? __ldcg(&parent[ca]) : ca;
+        const int32_t nb = wb ? __ldcg(&parent[cb]) : cb;
+        if (wa) {
+            if (ca > na) {
+                parent[pa] = na;
+                pa = ca;
+                ca = na;
+            } else {
+                wa = false;
+            }
+        }
+        if (wb) {
+            if (cb > nb) {
+                parent[pb] = nb;
+                pb = cb;
+                cb = nb;
+            } else {
+                wb = false;
+            }
+        }
+    }
+    ra = ca;
+    rb = cb;
+}
+
 // Retry cap of one link.  Debug builds read a lowered cap from the counter
 // block (set from TEC_DEBUG_LINK_CAP by the host), so a test can make the cap
 // run out on purpose; 0 there means the normal cap.
@@ -45,7 +79,8 @@ __device__ __forceinline__ int link_cap(const unsigned long long *ctr) {
 // the retry loop makes global progress; the cap only guards against a broken
 // forest and reports TEC_ETIMEOUT.
 __device__ __forceinline__ void uf_link(int32_t *parent, int32_t a, int32_t b, unsigned long long *ctr) {
-    int32_t ra = uf_find(parent, a), rb = uf_find(parent, b);
+    int32_t ra, rb;
+    uf_find2(parent, a, b, ra, rb);
     const int cap = link_cap(ctr);
     for (int it = 0; it < cap; ++it) {
         if (ra == rb) return;
@@ -53,8 +88,7 @@ __device__ __forceinline__ void uf_link(int32_t *parent, int32_t a, int32_t b, u
         const int32_t lo = ra > rb ? rb : ra;
         const int32_t old = atomicCAS(&parent[hi], hi, lo);
         if (old == hi) return;
-        ra = uf_find(parent, old);
-        rb = uf_find(parent, lo);
+        uf_find2(parent, old, lo, ra, rb);
     }
     flag_status(ctr, ST_TIMEOUT);
 }
@@ -66,7 +100,8 @@ namespace tec {
 // uf_link that also reports whether this call joined two different trees
 // (exactly one caller succeeds for each merge).
 __device__ __forceinline__ bool uf_link_merged(int32_t *parent, int32_t a, int32_t b, unsigned long long *ctr) {
-    int32_t ra = uf_find(parent, a), rb = uf_find(parent, b);
+    int32_t ra, rb;
+    uf_find2(parent, a, b, ra, rb);
     const int cap = link_cap(ctr);
     for (int it = 0; it < cap; ++it) {
         if (ra == rb) return false;
@@ -74,8 +109,7 @@ __device__ __forceinline__ bool uf_link_merged(int32_t *parent, int32_t a, int32
         const int32_t lo = ra > rb ? rb : ra;
         const int32_t old = atomicCAS(&parent[hi], hi, lo);
         if (old == hi) return true;
-        ra = uf_find(parent, old);
-        rb = uf_find(parent, lo);
+        uf_find2(parent, old, lo, ra, rb);
     }
     flag_status(ctr, ST_TIMEOUT);
     return false;

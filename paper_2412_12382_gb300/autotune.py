@@ -64,6 +64,7 @@ TUNABLES = {
     "ORIENT_FLAGS_MIN_BLOCKS": ("orient.cu", [1, 6, 7, 8]),  # register budget of the flag pass
     "ORIENT_GATHER_CG": ("orient.cu", [0, 1]),              # degree gathers bypass L1
     "PRUNE_SEG_ITEMS": ("prune.cu", [1, 2, 4, 8]),          # batched prune: items whose loads fly together
+    "PRUNE_SEG_PERSISTENT": ("prune.cu", [0, 1]),           # batched prune: tiles per block or persistent warps
 }
 
 

@@ -185,6 +185,8 @@ k_prune_bulk(const int32_t *__restrict__ ocol, const int32_t *__restrict__ deg, 
 }
 
 // Per-graph thresholds: the edge's graph is the segment of its source row.
+// One block per tile; used without a per-edge source table (the persistent
+// k_prune_seg_warps below is the default otherwise).
 // With a third or more of the edges kept the hooks dominate and want
 // occupancy: loading all eight items ahead (116 registers) took the
 // 500-graph batch from 1.95 to 4.2 ms.  Items in flight per group, chosen by
@@ -250,6 +252,70 @@ k_prune_seg(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const 
             const unsigned w = __ballot_sync(0xffffffffu, kp[b]);
             if (lane == 0 && jw < m) keep[jw >> 5] = w;
             kept += kp[b] ? 1 : 0;
+        }
+    }
+    kept = warp_sum(kept);
+    if (lane == 0) ws[threadIdx.x >> 5] = kept;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < TILE_THREADS / 32; ++w) tot += ws[w];
+        if (tot) atomicAdd(&ctr[C_KEPT], (unsigned long long)tot);
+    }
+}
+
+// k_prune_seg as a persistent kernel of independent warps: each warp walks
+// chunks of 256 consecutive edges (8 rounds of 32), chunk c, c + total warps,
+// ...; it finds the graphs of its chunk's first and last edge itself, so no
+// block barrier stands between chunks and a warp held up by long union-find
+// walks keeps only itself waiting, not the other warps of a block.  Needs the
+// per-edge source table.  Chosen by the autotuner (PRUNE_SEG_PERSISTENT).
+constexpr int PRUNE_SEG_PERSISTENT = 1;
+constexpr int PS_CHUNK = 256;
+
+__device__ __forceinline__ int seg_search(const int64_t *seg_off, int lo, int hi, int64_t x) {
+    while (lo < hi) {                            // last segment in [lo, hi] starting at or before x
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg_off[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <bool HOOK>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_prune_seg_warps(const int32_t *__restrict__ ocol, const int32_t *__restrict__ deg, const uint32_t *__restrict__ t,
+                  int64_t m, const int32_t *__restrict__ osrc, int measure, const int64_t *__restrict__ sp,
+                  const int64_t *__restrict__ sq, const int64_t *__restrict__ seg_off, int nseg,
+                  uint32_t *__restrict__ keep, int32_t *parent, unsigned long long *ctr) {
+    __shared__ int ws[TILE_THREADS / 32];
+    if (graph_bad(ctr)) return;
+    const unsigned lane = lane_id();
+    const int64_t warps = (int64_t)gridDim.x * (TILE_THREADS / 32);
+    const int64_t nchunks = ceil_div(m, PS_CHUNK);
+    int kept = 0;
+    for (int64_t c = (int64_t)blockIdx.x * (TILE_THREADS / 32) + (threadIdx.x >> 5); c < nchunks; c += warps) {
+        const int64_t j0 = c * PS_CHUNK;
+        const int64_t jl = (j0 + PS_CHUNK < m ? j0 + PS_CHUNK : m) - 1;
+        // lane 0 finds the graph of the first edge, lane 1 that of the last
+        const int mine = lane < 2 ? seg_search(seg_off, 0, nseg - 1, osrc[lane == 0 ? j0 : jl]) : 0;
+        const int s0 = __shfl_sync(0xffffffffu, mine, 0), s1 = __shfl_sync(0xffffffffu, mine, 1);
+        for (int i = 0; i < PS_CHUNK / 32; ++i) {
+            const int64_t jw = j0 + i * 32;
+            const int64_t j = jw + lane;
+            bool kp = false;
+            if (j < m) {
+                const int32_t u = osrc[j];
+                const int lo = seg_search(seg_off, s0, s1, u);
+                const int32_t v = ocol[j];
+                const int64_t s = (int64_t)deg[u] + deg[v];
+                const int64_t p = sp[lo], q = sq[lo];
+                kp = q > 0 && (needs_wide_dev(p, q) ? keep_edge<true>(measure, t[j], s, p, q)
+                                                    : keep_edge<false>(measure, t[j], s, p, q));
+                if (HOOK && kp) uf_link(parent, u, v, ctr);
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, kp);
+            if (lane == 0 && jw < m) keep[jw >> 5] = b;
+            kept += kp ? 1 : 0;
         }
     }
     kept = warp_sum(kept);
@@ -374,6 +440,16 @@ cudaError_t launch_prune_seg(const int64_t *ooff, const int32_t *ocol, const int
                              const int64_t *seg_off, int nseg, bool hook, uint32_t *keep, int32_t *parent,
                              unsigned long long *ctr, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
+    if (PRUNE_SEG_PERSISTENT && osrc) {
+        unsigned pgrid = 1;
+        cudaError_t e = hook ? persistent_grid(k_prune_seg_warps<true>, TILE_THREADS, 0, ceil_div(m, PS_CHUNK), &pgrid)
+                             : persistent_grid(k_prune_seg_warps<false>, TILE_THREADS, 0, ceil_div(m, PS_CHUNK), &pgrid);
+        if (e != cudaSuccess) return e;
+        if (hook) k_prune_seg_warps<true><<<pgrid, TILE_THREADS, 0, s>>>(ocol, deg, t, m, osrc, measure, sp, sq, seg_off, nseg, keep, parent, ctr);
+        else k_prune_seg_warps<false><<<pgrid, TILE_THREADS, 0, s>>>(ocol, deg, t, m, osrc, measure, sp, sq, seg_off, nseg, keep, parent, ctr);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     const unsigned grid = (unsigned)ceil_div(m, TILE);
     if (hook) k_prune_seg<true><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, osrc, measure, sp, sq, seg_off, nseg, keep, parent, ctr);
     else k_prune_seg<false><<<grid, TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, osrc, measure, sp, sq, seg_off, nseg, keep, parent, ctr);

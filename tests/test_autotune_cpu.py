@@ -18,7 +18,7 @@ def test_every_tunable_has_one_definition_and_safe_candidates():
         if name == "CORE_ORDER":                       # a choice of order, 0..2
             assert v in (0, 1, 2) and set(cands) <= {0, 1, 2}
             continue
-        if name == "ORIENT_GATHER_CG" or (name.startswith("ORIENT_") and name.endswith("_PERSISTENT")):  # a switch
+        if name == "ORIENT_GATHER_CG" or name.endswith("_PERSISTENT"):  # a switch
             assert v in (0, 1) and set(cands) == {0, 1}
             continue
         assert v > 0 and all(c > 0 for c in cands)

@@ -65,6 +65,7 @@ TUNABLES = {
     "ORIENT_GATHER_CG": ("orient.cu", [0, 1]),              # degree gathers bypass L1
     "PRUNE_SEG_ITEMS": ("prune.cu", [1, 2, 4, 8]),          # batched prune: items whose loads fly together
     "PRUNE_SEG_PERSISTENT": ("prune.cu", [0, 1]),           # batched prune: tiles per block or persistent warps
+    "FEAT_PERSISTENT": ("eval.cu", [0, 1]),                 # feature histogram: tiles per block or persistent warps
 }
 
 

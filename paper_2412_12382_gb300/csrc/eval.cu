@@ -26,6 +26,7 @@
 // with an older tag reads as empty, so the table is zeroed only when the tag
 // wraps, not per level.  Sizes use two plain counter arrays in turn: each
 // level's first pass zeroes the array the next level will use.
+#include "bulk.cuh"
 #include "tec_internal.cuh"
 
 namespace tec {
@@ -87,6 +88,87 @@ k_feat_hist(const int64_t *ooff, const int32_t *ocol, const int32_t *deg, const 
     }
     __syncthreads();
     if (one && threadIdx.x < NBINS && s_h[threadIdx.x]) atomicAdd(&hist[(int64_t)s0 * NBINS + threadIdx.x], s_h[threadIdx.x]);
+}
+
+// k_feat_hist as a persistent grid of independent warps, each with its own
+// shared-memory histogram and a contiguous share of 256-edge chunks: a warp
+// adds into its histogram while its chunks stay in one graph and flushes it
+// (64 global adds) when the graph changes, so there is no block barrier and
+// no contention between warps.  Needs the per-edge source table.  Chosen by
+// the autotuner (FEAT_PERSISTENT).
+constexpr int FEAT_PERSISTENT = 1;
+constexpr int FH_CHUNK = 256;
+
+__device__ __forceinline__ int seg_in(const int64_t *seg_off, int lo, int hi, int64_t x) {
+    while (lo < hi) {                            // last segment in [lo, hi] starting at or before x
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg_off[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(TILE_THREADS)
+k_feat_hist_warps(const int32_t *__restrict__ ocol, const int32_t *__restrict__ deg, const uint32_t *__restrict__ t,
+                  int64_t m, const int32_t *__restrict__ osrc, const int64_t *__restrict__ seg_off, int nseg,
+                  unsigned int *hist, unsigned long long *ctr) {
+    __shared__ unsigned int s_h[TILE_THREADS / 32][NBINS];
+    if (graph_bad(ctr)) return;
+    const unsigned lane = lane_id();
+    unsigned int *h = s_h[threadIdx.x >> 5];
+    h[lane] = 0u;
+    h[lane + 32] = 0u;
+    __syncwarp();
+    const int64_t nchunks = ceil_div(m, FH_CHUNK);
+    const int64_t warps = (int64_t)gridDim.x * (TILE_THREADS / 32);
+    const int64_t per = ceil_div(nchunks, warps);
+    const int64_t c0 = ((int64_t)blockIdx.x * (TILE_THREADS / 32) + (threadIdx.x >> 5)) * per;
+    const int64_t c1 = c0 + per < nchunks ? c0 + per : nchunks;
+    int cur = -1;                                // the graph whose counts h holds
+    auto flush = [&]() {
+        __syncwarp();
+        if (cur >= 0) {
+            for (int b = (int)lane; b < NBINS; b += 32)
+                if (h[b]) {
+                    atomicAdd(&hist[(int64_t)cur * NBINS + b], h[b]);
+                    h[b] = 0u;
+                }
+        }
+        __syncwarp();
+    };
+    for (int64_t c = c0; c < c1; ++c) {
+        const int64_t j0 = c * FH_CHUNK;
+        const int64_t jl = (j0 + FH_CHUNK < m ? j0 + FH_CHUNK : m) - 1;
+        int s0 = 0, s1 = 0;
+        if (seg_off) {                           // lane 0: graph of the first edge, lane 1: of the last
+            const int mine = lane < 2 ? seg_in(seg_off, 0, nseg - 1, osrc[lane == 0 ? j0 : jl]) : 0;
+            s0 = __shfl_sync(0xffffffffu, mine, 0);
+            s1 = __shfl_sync(0xffffffffu, mine, 1);
+        }
+        const bool one = s0 == s1;
+        if (one && s0 != cur) {
+            flush();
+            cur = s0;
+        }
+        for (int i = 0; i < FH_CHUNK / 32; ++i) {
+            const int64_t j = j0 + i * 32 + lane;
+            const bool valid = j < m;
+            int b = -1;
+            int32_t u = 0;
+            if (valid) {
+                u = osrc[j];
+                b = weight_bin(t[j], (int64_t)deg[u] + deg[ocol[j]]);
+            }
+            // bin 0 (edges in no triangle) is added once per warp
+            const unsigned zero = __ballot_sync(0xffffffffu, valid && b == 0);
+            if (one) {
+                if (lane == 0 && zero) atomicAdd(&h[0], (unsigned)__popc(zero));
+                if (valid && b > 0) atomicAdd(&h[b], 1u);
+            } else if (valid) {
+                atomicAdd(&hist[(int64_t)seg_in(seg_off, s0, s1, u) * NBINS + b], 1u);
+            }
+        }
+    }
+    flush();
 }
 
 // One warp per graph: 64 normalised bins, ln(2m/n), ln(m).
@@ -519,9 +601,15 @@ cudaError_t launch_features(const int64_t *ooff, const int32_t *ocol, const int3
     const int ns = seg_off ? nseg : 1;
     cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)ns * NBINS * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    if (m > 0)
+    if (m > 0 && FEAT_PERSISTENT && osrc) {
+        unsigned grid = 1;
+        e = persistent_grid(k_feat_hist_warps, TILE_THREADS, 0, ceil_div(m, FH_CHUNK), &grid);
+        if (e != cudaSuccess) return e;
+        k_feat_hist_warps<<<grid, TILE_THREADS, 0, s>>>(ocol, deg, t, m, osrc, seg_off, ns, hist, ctr);
+    } else if (m > 0) {
         k_feat_hist<<<(unsigned)ceil_div(m, TILE), TILE_THREADS, 0, s>>>(ooff, ocol, deg, t, n, m, orows, osrc, seg_off, ns,
                                                                          hist, ctr);
+    }
     k_feat_final<<<(unsigned)ceil_div((int64_t)ns * 32, 256), 256, 0, s>>>(hist, seg_off, ns, n, feat);
     count_launches(m > 0 ? 2 : 1);
     return cudaGetLastError();
